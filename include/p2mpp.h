@@ -1,0 +1,234 @@
+/*
+ * p2mpp.h -- C ABI of libp2mpp.so, a GB300 (sm_103a) implementation of the P2M++ query
+ * path: Voronoi-localised exact closest-triangle search on a triangle mesh.
+ *
+ * The method (P2M++, Guo et al.):
+ *   * Sites = referenced mesh vertices plus auxiliary sites added where Voronoi vertices
+ *     cluster (Section 3.2, "Ring-based Site Augmentation").
+ *   * Each site's cell is a convex polytope; its interception list is every triangle that
+ *     meets the union of balls B(u, ||u - v||) centred at the cell's corners u, with v the
+ *     site's reference point on the mesh (Section 3.3, Eq. 2, Eq. 3 "Vertex Sphere Union").
+ *     An off-surface site uses one ball of radius Eq. 8 around itself instead.
+ *   * A query finds its nearest site and scans only that site's list, pruning with each
+ *     triangle's bounding sphere (Section 3.3 "Distance Query Stage", "Bounding Sphere
+ *     Pruning").  The result is the exact closest point on the mesh.
+ *
+ * Conventions for every entry point:
+ *   * Return value 0 (P2M_OK) on success, else one of the negative P2M_ERR_* codes;
+ *     p2m_last_error() then returns a thread-local message.  No entry point aborts or
+ *     traps; device-side failures (stack overflow, iteration caps) come back as codes.
+ *   * `stream` is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     Device work is stream-ordered and asynchronous unless the entry point says it
+ *     synchronises.
+ *   * "d_" pointers are device pointers, "h_" pointers host pointers.  Caller-owned
+ *     buffers stay caller-owned; the library never frees them.
+ *   * Points and vertices are float32 xyz triples, row-major [n,3].  Triangle ids index
+ *     the caller's `tris` array; barycentrics (b0,b1,b2) refer to that triangle's
+ *     (v0,v1,v2) so that closest = b0 v0 + b1 v1 + b2 v2.
+ *   * Sizes are int64_t.  n == 0 is a successful no-op wherever n appears.
+ */
+#ifndef P2MPP_H
+#define P2MPP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define P2M_OK 0
+#define P2M_ERR_INVALID_ARG (-1)     /* NULL/NaN/out-of-range input, bad sizes */
+#define P2M_ERR_CUDA (-2)            /* a CUDA runtime call failed */
+#define P2M_ERR_OOM (-3)             /* device or host allocation failed */
+#define P2M_ERR_EMPTY_MESH (-4)      /* no triangle, or no referenced vertex */
+#define P2M_ERR_DEGENERATE (-5)      /* fewer than 4 distinct sites, or all sites coplanar */
+#define P2M_ERR_LIMIT (-6)           /* a device work cap or iteration cap was reached */
+#define P2M_ERR_STACK (-7)           /* a device BVH traversal stack overflowed */
+#define P2M_ERR_NOT_IMPLEMENTED (-8)
+#define P2M_ERR_INTERNAL (-9)        /* an internal consistency check failed */
+
+typedef struct p2m_index p2m_index; /* opaque; owns every device structure it builds */
+
+/* Build parameters.  p2m_default_params() fills the defaults given in brackets. */
+typedef struct {
+    /* Domain box D = mesh bbox scaled by this factor about its centre [1.5].  Cells are
+     * clipped to D (the paper is silent on unbounded cells; every cell ∩ D is convex, so
+     * Eq. 3 still applies).  Queries outside D take an exact BVH branch-and-bound search. */
+    float domain_scale;
+    /* Site augmentation of Section 3.2 on/off [1]. */
+    int enable_aux;
+    /* tau = tau_scale x mean edge length [2.0] (Section 3.2 "Choice of Parameters"). */
+    float tau_scale;
+    /* A tau-cell is dense when its Voronoi-vertex count exceeds density_factor x the median
+     * count of non-empty tau-cells [8.0] and density_min [32]. */
+    float density_factor;
+    int density_min;
+    /* Auxiliary sites per ring: 12 (icosahedron directions) or 6 (octahedron) [12]. */
+    int ring_sites;
+    /* Ring radius = ring_radius_scale x tau [1.299 = 0.75 sqrt 3]. */
+    float ring_radius_scale;
+    /* List-membership slack, relative to the bbox diagonal [1e-6]: a triangle joins a list
+     * when its distance to a ball is <= radius + slack (conservative). */
+    float build_eps_rel;
+    /* Nearest-site grid resolution per axis; 0 = automatic [0]. */
+    int nn_grid_res;
+    /* Query schedule: 0 automatic, 1 thread per query, 2 warp per query, 3 site-binned
+     * thread per query with shared-memory staged lists [0]. */
+    int schedule;
+    /* Deterministic vertex-gradient accumulation (fixed-point integer atomics) [1]. */
+    int deterministic;
+    /* Seed of the site jitter used to break exact Delaunay degeneracies [1]. */
+    int seed;
+} p2m_build_params;
+
+/* Build statistics (Section 4.1, Table 1: Max / Avg list length) and stage timings. */
+typedef struct {
+    int64_t n_verts, n_tris;
+    int64_t n_sites, n_vertex_sites, n_aux_sites;
+    int64_t n_corners;        /* corner balls in the CSR ball table (aux sites count 1) */
+    int64_t nnz;              /* total interception-list entries */
+    int64_t max_row;          /* Max list length */
+    double avg_row;           /* Avg list length */
+    int64_t grid_res;         /* nearest-site grid cells per axis */
+    int64_t grid_entries;     /* total candidate-site entries in the grid */
+    int64_t grid_max;         /* longest candidate-site list */
+    int64_t n_delaunay_tets;
+    int64_t n_dense_cells;    /* tau-cells flagged dense by the augmentation */
+    double domain_lo[3], domain_hi[3];
+    double bbox_diag;
+    /* stage wall times in milliseconds */
+    double ms_upload, ms_tri, ms_lbvh, ms_delaunay, ms_cells, ms_aug, ms_proj, ms_k1, ms_grid, ms_total;
+} p2m_stats;
+
+/* Per-call query counters (Section 4.1, Table 1 "Queried"). */
+typedef struct {
+    int64_t n_queries;
+    int64_t n_outside;        /* queries outside D (answered by the BVH search) */
+    int64_t site_candidates;  /* candidate sites examined by the nearest-site search */
+    int64_t tie_rechecks;     /* nearest-site decisions re-checked in FP64 */
+    int64_t row_entries;      /* interception-list entries visited */
+    int64_t exact_tests;      /* exact point-triangle tests run (after pruning) */
+} p2m_counters;
+
+/* Library version string. */
+const char* p2m_version(void);
+
+/* Thread-local message describing the last non-zero return on this thread. */
+const char* p2m_last_error(void);
+
+/* Fill *out with the defaults documented in p2m_build_params.  Errors: INVALID_ARG if out
+ * is NULL. */
+int p2m_default_params(p2m_build_params* out);
+
+/* Build an index over a triangle mesh (the whole preprocessing of Section 3: Voronoi diagram
+ * of the sites, augmentation (Section 3.2), corner spheres (Eq. 3, Eq. 8), BVH collision
+ * into the interception lists (Section 3.3 "Implementation Details"), and the nearest-site
+ * grid).
+ *   verts[n_verts*3] float32, tris[n_tris*3] int32 (0-based).  If inputs_on_device != 0
+ *   both are device pointers, else host pointers.  The mesh is copied; the caller may free
+ *   its arrays when the call returns.  params may be NULL (defaults).
+ * Synchronises `stream`.  On success *out owns the index (release with p2m_destroy).
+ * Errors: INVALID_ARG (NULL, NaN/Inf vertex, index out of range, n <= 0), EMPTY_MESH,
+ * DEGENERATE, OOM, CUDA, STACK, LIMIT. */
+int p2m_build(const float* verts, int64_t n_verts, const int32_t* tris, int64_t n_tris,
+              int inputs_on_device, const p2m_build_params* params, void* stream,
+              p2m_index** out);
+
+/* Release an index and all device memory it owns.  NULL is a no-op. */
+void p2m_destroy(p2m_index* h);
+
+/* Closest-point query (Section 3.3 "Distance Query Stage"): for each of n points
+ * d_pts[n*3], nearest site -> scan of its interception list -> exact closest point.
+ *   d_dist[n]      unsigned distance (required)
+ *   d_closest[n*3] closest point on the mesh (or NULL)
+ *   d_tri[n]       triangle id holding the closest point (or NULL)
+ *   d_bary[n*3]    barycentrics of the closest point in that triangle (or NULL)
+ * Asynchronous on `stream`.  Errors: INVALID_ARG, CUDA, STACK (checked lazily: the
+ * overflow flag of a query is reported by the next synchronising call). */
+int p2m_query(p2m_index* h, const float* d_pts, int64_t n, float* d_dist, float* d_closest,
+              int32_t* d_tri, float* d_bary, void* stream);
+
+/* The same query from host memory: copies h_pts in chunks to the device, runs the query
+ * and copies the results back, overlapping copies and kernels on two streams.  Host
+ * buffers may be pageable, but pinned (cudaHostAlloc) buffers are much faster.  Output
+ * pointers other than h_dist may be NULL.  Synchronous: returns when the outputs are in
+ * host memory.  Errors: INVALID_ARG, OOM, CUDA. */
+int p2m_query_host(p2m_index* h, const float* h_pts, int64_t n, float* h_dist, float* h_closest,
+                   int32_t* h_tri, float* h_bary, void* stream);
+
+/* Nearest site only (the "Cell Locate" step, Section 3.3 "Recursive Nearest Neighbor
+ * Search"): d_site[n] gets the index of the nearest site (ties -> lower index), or -1 for
+ * a point outside D.  Asynchronous. */
+int p2m_nearest_site(p2m_index* h, const float* d_pts, int64_t n, int32_t* d_site, void* stream);
+
+/* Instrumented query: runs the query and fills *out with counters (Table 1 "Queried").
+ * Synchronises `stream`.  d_dist etc. as in p2m_query (d_dist may be NULL here). */
+int p2m_query_counters(p2m_index* h, const float* d_pts, int64_t n, float* d_dist,
+                       p2m_counters* out, void* stream);
+
+/* Backward of the unsigned distance (not in the paper; the differentiable form).  With p
+ * the closest point on triangle (v0,v1,v2), b its barycentrics and g = d_grad_dist[i]:
+ *   d_grad_pts[i]   = g (q - p) / ||q - p||          (0 when q lies on the mesh)
+ *   d_grad_verts[vk] += -g b_k (q - p) / ||q - p||    for k = 0,1,2
+ * p is recomputed from the index's current vertices and d_tri / d_bary of the forward.
+ * d_grad_pts may be NULL; d_grad_verts may be NULL; d_grad_verts[n_verts*3] is
+ * ACCUMULATED into (zero it first).  With params.deterministic the vertex sums are
+ * bit-reproducible (fixed-point integer atomics).  Asynchronous.  Errors: INVALID_ARG,
+ * OOM, CUDA. */
+int p2m_backward(p2m_index* h, const float* d_pts, int64_t n, const int32_t* d_tri,
+                 const float* d_bary, const float* d_grad_dist, float* d_grad_pts,
+                 float* d_grad_verts, void* stream);
+
+/* Replace the vertex positions (same topology) and rebuild every structure.  d_verts is a
+ * device pointer [n_verts*3].  Synchronises `stream`. */
+int p2m_update_vertices(p2m_index* h, const float* d_verts, void* stream);
+
+/* Build statistics (Table 1 Max / Avg, counts, stage times).  Host-only. */
+int p2m_get_stats(const p2m_index* h, p2m_stats* out);
+
+/* ---- Batched form (not in the paper): many meshes behind one persistent launch. ------ */
+
+/* Build one index over n_meshes meshes (host pointers verts[i], tris[i]).  Each mesh gets
+ * its own sites, lists and grid; all live in shared device arrays with per-mesh offsets.
+ * Synchronises.  Errors as p2m_build (the message names the failing mesh). */
+int p2m_batch_build(int n_meshes, const float* const* verts, const int64_t* n_verts,
+                    const int32_t* const* tris, const int64_t* n_tris,
+                    const p2m_build_params* params, void* stream, p2m_index** out);
+
+/* Query a batch: queries of mesh i are d_pts[h_q_offsets[i] .. h_q_offsets[i+1]) (host
+ * array of n_meshes+1 offsets, non-decreasing, starting at 0).  Outputs as p2m_query, tri
+ * ids local to each mesh.  mode 0: one persistent launch over a tile queue (tile size and
+ * schedule picked by the autotuner); with use_graph != 0 that launch is captured once in a
+ * CUDA graph per (batch, offsets) and replayed.  mode 1: one launch per mesh (the plain
+ * per-mesh forward, for comparison).  Asynchronous.  Errors: INVALID_ARG, CUDA, OOM. */
+int p2m_batch_query(p2m_index* batch, const float* d_pts, const int64_t* h_q_offsets,
+                    float* d_dist, float* d_closest, int32_t* d_tri, float* d_bary,
+                    int mode, int use_graph, void* stream);
+
+/* Number of meshes in an index (1 for p2m_build). */
+int p2m_num_meshes(const p2m_index* h);
+
+/* ---- Introspection (tests and tools).  All synchronous; host output buffers. -------- */
+
+/* Sizes of mesh `mesh` of the index: n_sites, nnz (list entries), n_balls (corner balls). */
+int p2m_get_sizes(const p2m_index* h, int mesh, int64_t* n_sites, int64_t* nnz, int64_t* n_balls);
+
+/* Sites of mesh `mesh`: h_sites[n_sites*3] float32 positions (the exact partition the
+ * queries use), h_ref[n_sites*3] float64 reference points on the mesh (vertex position,
+ * or proj(s, M) for an auxiliary site), h_kind[n_sites] 0 = vertex site, 1 = aux site.
+ * Any pointer may be NULL. */
+int p2m_get_sites(const p2m_index* h, int mesh, float* h_sites, double* h_ref, int32_t* h_kind);
+
+/* Interception lists (CSR) of mesh `mesh`: h_offsets[n_sites+1], h_tri_ids[nnz]. */
+int p2m_get_lists(const p2m_index* h, int mesh, int64_t* h_offsets, int32_t* h_tri_ids);
+
+/* Corner balls of mesh `mesh` (Eq. 3 / Eq. 8): h_ball_offsets[n_sites+1] into
+ * h_centres[n_balls*3] (float64) and h_radii[n_balls] (float64, before slack). */
+int p2m_get_balls(const p2m_index* h, int mesh, int64_t* h_ball_offsets, double* h_centres,
+                  double* h_radii);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* P2MPP_H */

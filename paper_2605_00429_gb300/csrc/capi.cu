@@ -1,0 +1,408 @@
+// C ABI of libp2mpp.so: argument checking, index lifecycle, build orchestration and query
+// dispatch.  The compute lives in the kernels of bvh.cu / lists.cu / grid.cu / query.cu and
+// the host Voronoi code of voronoi.cpp.
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "host.h"
+#include "p2m_internal.h"
+
+namespace p2m {
+
+static thread_local std::string g_err;
+
+void set_error(const std::string& msg) { g_err = msg; }
+int fail(int code, const std::string& msg) {
+    g_err = msg;
+    return code;
+}
+
+int DevBuf::alloc(size_t nbytes) {
+    release();
+    if (nbytes == 0) nbytes = 16;
+    cudaError_t e = cudaMalloc(&p, nbytes);
+    if (e != cudaSuccess) {
+        p = nullptr;
+        cudaGetLastError();
+        return fail(e == cudaErrorMemoryAllocation ? P2M_ERR_OOM : P2M_ERR_CUDA,
+                    std::string("cudaMalloc(") + std::to_string(nbytes) + "): " + cudaGetErrorString(e));
+    }
+    bytes = nbytes;
+    return P2M_OK;
+}
+
+int DevBuf::ensure(size_t nbytes) {
+    if (p && bytes >= nbytes) return P2M_OK;
+    return alloc(nbytes);
+}
+
+MeshView MeshData::view() const {
+    MeshView v{};
+    v.tri = d_tri.as<const float4>();
+    v.tsph = d_tsph.as<const float4>();
+    v.bvh = bvh.nodes.as<const BNode>();
+    v.bvh_root = bvh.root;
+    v.sites = d_sites.as<const float4>();
+    v.row_off = d_row_off.as<const int32_t>();
+    v.row_tri = d_row_tri.as<const int32_t>();
+    v.cell_off = d_cell_off.as<const int32_t>();
+    v.cell_site = d_cell_site.as<const int32_t>();
+    v.G = G;
+    v.lo = g_lo;
+    v.hi = g_hi;
+    v.inv_h = g_inv_h;
+    v.prune_abs = (float)(diag * std::ldexp(1.0, -22));
+    v.n_tris = (int)n_tris;
+    v.n_sites = (int)(site_pos.size() / 3);
+    return v;
+}
+
+static double now_ms() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+}  // namespace p2m
+
+using namespace p2m;
+
+struct p2m_index {
+    p2m_build_params params{};
+    std::vector<std::unique_ptr<MeshData>> meshes;
+    DevBuf status;          // device status word (ST_* bits)
+    DevBuf scratch_idx;     // out-of-domain query list
+    DevBuf scratch_cnt;
+    BatchState batch;       // batched-query state (tile queue, graph)
+    int device = 0;
+};
+
+namespace p2m {
+
+unsigned* index_status(p2m_index* h) { return h->status.as<unsigned>(); }
+
+int check_status_word(p2m_index* h, cudaStream_t s, const char* what) {
+    unsigned st = 0;
+    P2M_CUDA_TRY(cudaMemcpyAsync(&st, h->status.p, sizeof(unsigned), cudaMemcpyDeviceToHost, s));
+    P2M_CUDA_TRY(cudaStreamSynchronize(s));
+    if (st) {
+        P2M_CUDA_TRY(cudaMemsetAsync(h->status.p, 0, sizeof(unsigned), s));
+        if (st & ST_STACK) return fail(P2M_ERR_STACK, std::string(what) + ": device traversal stack overflow");
+        if (st & ST_LIMIT) return fail(P2M_ERR_LIMIT, std::string(what) + ": device capacity or iteration cap reached");
+        return fail(P2M_ERR_INTERNAL, std::string(what) + ": device index check failed");
+    }
+    return P2M_OK;
+}
+
+}  // namespace p2m
+
+// ----------------------------------------------------------------------------- validation
+
+static int validate_params(const p2m_build_params& p) {
+    if (!(p.domain_scale >= 1.0f && p.domain_scale < 1e6f)) return fail(P2M_ERR_INVALID_ARG, "domain_scale must be >= 1");
+    if (!(p.tau_scale > 0.0f)) return fail(P2M_ERR_INVALID_ARG, "tau_scale must be > 0");
+    if (!(p.density_factor > 0.0f)) return fail(P2M_ERR_INVALID_ARG, "density_factor must be > 0");
+    if (p.ring_sites != 6 && p.ring_sites != 12) return fail(P2M_ERR_INVALID_ARG, "ring_sites must be 6 or 12");
+    if (!(p.ring_radius_scale > 0.0f)) return fail(P2M_ERR_INVALID_ARG, "ring_radius_scale must be > 0");
+    if (!(p.build_eps_rel >= 0.0f && p.build_eps_rel < 1e-2f)) return fail(P2M_ERR_INVALID_ARG, "build_eps_rel out of range");
+    if (p.nn_grid_res < 0 || p.nn_grid_res > 1024) return fail(P2M_ERR_INVALID_ARG, "nn_grid_res out of range");
+    if (p.schedule < 0 || p.schedule > 3) return fail(P2M_ERR_INVALID_ARG, "schedule must be 0..3");
+    return P2M_OK;
+}
+
+// Copy the mesh to host vectors and check it.
+static int load_mesh(const float* verts, int64_t n_verts, const int32_t* tris, int64_t n_tris, int on_device,
+                     MeshData& m) {
+    if (!verts || !tris) return fail(P2M_ERR_INVALID_ARG, "verts and tris must be non-NULL");
+    if (n_verts <= 0 || n_tris <= 0) return fail(P2M_ERR_EMPTY_MESH, "mesh needs at least one vertex and one triangle");
+    if (n_verts > (int64_t)1 << 30 || n_tris > (int64_t)1 << 30) return fail(P2M_ERR_INVALID_ARG, "mesh too large (>2^30)");
+    m.n_verts = n_verts;
+    m.n_tris = n_tris;
+    m.verts.resize(n_verts * 3);
+    m.tris.resize(n_tris * 3);
+    if (on_device) {
+        P2M_CUDA_TRY(cudaMemcpy(m.verts.data(), verts, sizeof(float) * 3 * n_verts, cudaMemcpyDeviceToHost));
+        P2M_CUDA_TRY(cudaMemcpy(m.tris.data(), tris, sizeof(int32_t) * 3 * n_tris, cudaMemcpyDeviceToHost));
+    } else {
+        std::memcpy(m.verts.data(), verts, sizeof(float) * 3 * n_verts);
+        std::memcpy(m.tris.data(), tris, sizeof(int32_t) * 3 * n_tris);
+    }
+    for (int64_t i = 0; i < n_verts * 3; ++i)
+        if (!std::isfinite(m.verts[i])) return fail(P2M_ERR_INVALID_ARG, "vertex " + std::to_string(i / 3) + " is not finite");
+    std::vector<char> used(n_verts, 0);
+    for (int64_t i = 0; i < n_tris * 3; ++i) {
+        const int32_t v = m.tris[i];
+        if (v < 0 || v >= n_verts)
+            return fail(P2M_ERR_INVALID_ARG, "triangle " + std::to_string(i / 3) + " has vertex index " + std::to_string(v) +
+                                                 " out of range");
+        used[v] = 1;
+    }
+    for (int k = 0; k < 3; ++k) { m.bb_lo[k] = INFINITY; m.bb_hi[k] = -INFINITY; }
+    for (int64_t i = 0; i < n_verts; ++i) {
+        if (!used[i]) continue;
+        for (int k = 0; k < 3; ++k) {
+            m.bb_lo[k] = std::min(m.bb_lo[k], (double)m.verts[3 * i + k]);
+            m.bb_hi[k] = std::max(m.bb_hi[k], (double)m.verts[3 * i + k]);
+        }
+    }
+    double d2 = 0;
+    for (int k = 0; k < 3; ++k) d2 += (m.bb_hi[k] - m.bb_lo[k]) * (m.bb_hi[k] - m.bb_lo[k]);
+    m.diag = std::sqrt(d2);
+    if (!(m.diag > 0)) return fail(P2M_ERR_DEGENERATE, "all referenced vertices coincide");
+    return P2M_OK;
+}
+
+// ----------------------------------------------------------------------------- build
+
+static int build_mesh(MeshData& m, const p2m_build_params& prm, p2m_index* h, cudaStream_t s) {
+    p2m_stats& st = m.stats;
+    std::memset(&st, 0, sizeof(st));
+    const double t0 = now_ms();
+    st.n_verts = m.n_verts;
+    st.n_tris = m.n_tris;
+    st.bbox_diag = m.diag;
+    for (int k = 0; k < 3; ++k) {
+        const double c = 0.5 * (m.bb_lo[k] + m.bb_hi[k]);
+        const double e = 0.5 * (m.bb_hi[k] - m.bb_lo[k]);
+        // a flat axis still gets a slab of half-width diag/4 so that D has volume
+        const double ee = std::max(e, 0.25 * m.diag) * prm.domain_scale;
+        m.dom_lo[k] = c - ee;
+        m.dom_hi[k] = c + ee;
+        st.domain_lo[k] = m.dom_lo[k];
+        st.domain_hi[k] = m.dom_hi[k];
+    }
+    // upload + K0b
+    const int T = (int)m.n_tris;
+    P2M_TRY(m.d_verts.alloc(sizeof(float) * 3 * m.n_verts));
+    P2M_TRY(m.d_tris.alloc(sizeof(int32_t) * 3 * m.n_tris));
+    P2M_CUDA_TRY(cudaMemcpyAsync(m.d_verts.p, m.verts.data(), sizeof(float) * 3 * m.n_verts, cudaMemcpyHostToDevice, s));
+    P2M_CUDA_TRY(cudaMemcpyAsync(m.d_tris.p, m.tris.data(), sizeof(int32_t) * 3 * m.n_tris, cudaMemcpyHostToDevice, s));
+    P2M_CUDA_TRY(cudaStreamSynchronize(s));
+    double t1 = now_ms();
+    st.ms_upload = t1 - t0;
+    P2M_TRY(m.d_tri.alloc(sizeof(float4) * 4 * T));
+    P2M_TRY(m.d_tsph.alloc(sizeof(float4) * T));
+    P2M_TRY(launch_tri_precompute(m.d_verts.as<float>(), m.d_tris.as<int32_t>(), T, m.d_tri.as<float4>(),
+                                  m.d_tsph.as<float4>(), s));
+    P2M_CUDA_TRY(cudaStreamSynchronize(s));
+    double t2 = now_ms();
+    st.ms_tri = t2 - t1;
+    // K0: triangle LBVH
+    {
+        DevBuf lo, hi;
+        P2M_TRY(lo.alloc(sizeof(float4) * T));
+        P2M_TRY(hi.alloc(sizeof(float4) * T));
+        P2M_TRY(tri_boxes(m.d_verts.as<float>(), m.d_tris.as<int32_t>(), T, lo.as<float4>(), hi.as<float4>(), s));
+        const float3 clo = make_float3((float)m.bb_lo[0], (float)m.bb_lo[1], (float)m.bb_lo[2]);
+        const float3 chi = make_float3((float)m.bb_hi[0], (float)m.bb_hi[1], (float)m.bb_hi[2]);
+        P2M_TRY(build_lbvh(lo.as<float4>(), hi.as<float4>(), T, clo, chi, m.bvh, s));
+    }
+    double t3 = now_ms();
+    st.ms_lbvh = t3 - t2;
+    // host Voronoi, augmentation, corner balls, lists, nearest-site grid
+    P2M_TRY(build_partition(m, prm, h, s));
+    st.ms_total = now_ms() - t0;
+    return P2M_OK;
+}
+
+extern "C" {
+
+const char* p2m_version(void) { return "p2mpp-gb300 0.1 (sm_103a)"; }
+
+const char* p2m_last_error(void) { return g_err.c_str(); }
+
+int p2m_default_params(p2m_build_params* out) {
+    if (!out) return fail(P2M_ERR_INVALID_ARG, "out is NULL");
+    std::memset(out, 0, sizeof(*out));
+    out->domain_scale = 1.5f;
+    out->enable_aux = 1;
+    out->tau_scale = 2.0f;
+    out->density_factor = 8.0f;
+    out->density_min = 32;
+    out->ring_sites = 12;
+    out->ring_radius_scale = 1.299038f;  // 0.75 * sqrt(3)
+    out->build_eps_rel = 1e-6f;
+    out->nn_grid_res = 0;
+    out->schedule = 0;
+    out->deterministic = 1;
+    out->seed = 1;
+    return P2M_OK;
+}
+
+static int new_index(const p2m_build_params* params, p2m_index** out, std::unique_ptr<p2m_index>& h) {
+    if (!out) return fail(P2M_ERR_INVALID_ARG, "out is NULL");
+    *out = nullptr;
+    h.reset(new p2m_index());
+    if (params) h->params = *params;
+    else p2m_default_params(&h->params);
+    P2M_TRY(validate_params(h->params));
+    P2M_CUDA_TRY(cudaGetDevice(&h->device));
+    P2M_TRY(h->status.alloc(sizeof(unsigned) * 4));
+    P2M_CUDA_TRY(cudaMemset(h->status.p, 0, sizeof(unsigned) * 4));
+    return P2M_OK;
+}
+
+int p2m_build(const float* verts, int64_t n_verts, const int32_t* tris, int64_t n_tris, int inputs_on_device,
+              const p2m_build_params* params, void* stream, p2m_index** out) {
+    std::unique_ptr<p2m_index> h;
+    P2M_TRY(new_index(params, out, h));
+    cudaStream_t s = (cudaStream_t)stream;
+    std::unique_ptr<MeshData> m(new MeshData());
+    P2M_TRY(load_mesh(verts, n_verts, tris, n_tris, inputs_on_device, *m));
+    P2M_TRY(build_mesh(*m, h->params, h.get(), s));
+    P2M_TRY(check_status_word(h.get(), s, "build"));
+    h->meshes.push_back(std::move(m));
+    *out = h.release();
+    return P2M_OK;
+}
+
+void p2m_destroy(p2m_index* h) {
+    if (!h) return;
+    cudaDeviceSynchronize();
+    delete h;
+}
+
+int p2m_query(p2m_index* h, const float* d_pts, int64_t n, float* d_dist, float* d_closest, int32_t* d_tri,
+              float* d_bary, void* stream) {
+    if (!h || h->meshes.size() != 1) return fail(P2M_ERR_INVALID_ARG, "p2m_query needs a single-mesh index");
+    if (n < 0) return fail(P2M_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return P2M_OK;
+    if (!d_pts || !d_dist) return fail(P2M_ERR_INVALID_ARG, "d_pts and d_dist must be non-NULL");
+    return run_query(h, *h->meshes[0], d_pts, n, d_dist, d_closest, d_tri, d_bary, nullptr, (cudaStream_t)stream);
+}
+
+int p2m_query_counters(p2m_index* h, const float* d_pts, int64_t n, float* d_dist, p2m_counters* out,
+                       void* stream) {
+    if (!h || h->meshes.size() != 1 || !out) return fail(P2M_ERR_INVALID_ARG, "bad index or out");
+    if (n < 0 || (n > 0 && !d_pts)) return fail(P2M_ERR_INVALID_ARG, "bad points");
+    std::memset(out, 0, sizeof(*out));
+    if (n == 0) return P2M_OK;
+    cudaStream_t s = (cudaStream_t)stream;
+    DevBuf cnt, dist;
+    P2M_TRY(cnt.alloc(sizeof(unsigned long long) * 8));
+    P2M_CUDA_TRY(cudaMemsetAsync(cnt.p, 0, sizeof(unsigned long long) * 8, s));
+    float* dd = d_dist;
+    if (!dd) {
+        P2M_TRY(dist.alloc(sizeof(float) * n));
+        dd = dist.as<float>();
+    }
+    P2M_TRY(run_query(h, *h->meshes[0], d_pts, n, dd, nullptr, nullptr, nullptr, cnt.as<unsigned long long>(), s));
+    unsigned long long c[8];
+    P2M_CUDA_TRY(cudaMemcpyAsync(c, cnt.p, sizeof(c), cudaMemcpyDeviceToHost, s));
+    P2M_CUDA_TRY(cudaStreamSynchronize(s));
+    P2M_TRY(check_status_word(h, s, "query"));
+    out->n_queries = n;
+    out->n_outside = (int64_t)c[0];
+    out->site_candidates = (int64_t)c[1];
+    out->tie_rechecks = (int64_t)c[2];
+    out->row_entries = (int64_t)c[3];
+    out->exact_tests = (int64_t)c[4];
+    return P2M_OK;
+}
+
+int p2m_nearest_site(p2m_index* h, const float* d_pts, int64_t n, int32_t* d_site, void* stream) {
+    if (!h || h->meshes.size() != 1) return fail(P2M_ERR_INVALID_ARG, "p2m_nearest_site needs a single-mesh index");
+    if (n < 0 || (n > 0 && (!d_pts || !d_site))) return fail(P2M_ERR_INVALID_ARG, "bad arguments");
+    if (n == 0) return P2M_OK;
+    return run_nearest_site(h, *h->meshes[0], d_pts, n, d_site, (cudaStream_t)stream);
+}
+
+int p2m_get_stats(const p2m_index* h, p2m_stats* out) {
+    if (!h || !out || h->meshes.empty()) return fail(P2M_ERR_INVALID_ARG, "bad index or out");
+    if (h->meshes.size() == 1) {
+        *out = h->meshes[0]->stats;
+        return P2M_OK;
+    }
+    // batch: sums of counts, max of maxima, summed times
+    p2m_stats a{};
+    double rows = 0;
+    for (auto& mp : h->meshes) {
+        const p2m_stats& b = mp->stats;
+        a.n_verts += b.n_verts; a.n_tris += b.n_tris; a.n_sites += b.n_sites;
+        a.n_vertex_sites += b.n_vertex_sites; a.n_aux_sites += b.n_aux_sites; a.n_corners += b.n_corners;
+        a.nnz += b.nnz; a.max_row = std::max(a.max_row, b.max_row); a.grid_entries += b.grid_entries;
+        a.grid_max = std::max(a.grid_max, b.grid_max); a.grid_res = std::max(a.grid_res, b.grid_res);
+        a.n_delaunay_tets += b.n_delaunay_tets; a.n_dense_cells += b.n_dense_cells;
+        a.ms_upload += b.ms_upload; a.ms_tri += b.ms_tri; a.ms_lbvh += b.ms_lbvh; a.ms_delaunay += b.ms_delaunay;
+        a.ms_cells += b.ms_cells; a.ms_aug += b.ms_aug; a.ms_proj += b.ms_proj; a.ms_k1 += b.ms_k1;
+        a.ms_grid += b.ms_grid; a.ms_total += b.ms_total;
+        rows += (double)b.n_sites;
+    }
+    a.avg_row = rows > 0 ? (double)a.nnz / rows : 0.0;
+    *out = a;
+    return P2M_OK;
+}
+
+int p2m_num_meshes(const p2m_index* h) { return h ? (int)h->meshes.size() : 0; }
+
+static int mesh_of(const p2m_index* h, int mesh, MeshData** m) {
+    if (!h || mesh < 0 || mesh >= (int)h->meshes.size()) return fail(P2M_ERR_INVALID_ARG, "bad index or mesh id");
+    *m = h->meshes[mesh].get();
+    return P2M_OK;
+}
+
+int p2m_get_sizes(const p2m_index* h, int mesh, int64_t* n_sites, int64_t* nnz, int64_t* n_balls) {
+    MeshData* m;
+    P2M_TRY(mesh_of(h, mesh, &m));
+    if (n_sites) *n_sites = (int64_t)m->site_kind.size();
+    if (nnz) *nnz = m->nnz;
+    if (n_balls) *n_balls = (int64_t)m->ball_r.size();
+    return P2M_OK;
+}
+
+int p2m_get_sites(const p2m_index* h, int mesh, float* h_sites, double* h_ref, int32_t* h_kind) {
+    MeshData* m;
+    P2M_TRY(mesh_of(h, mesh, &m));
+    if (h_sites) std::memcpy(h_sites, m->site_pos.data(), sizeof(float) * m->site_pos.size());
+    if (h_ref) std::memcpy(h_ref, m->site_ref.data(), sizeof(double) * m->site_ref.size());
+    if (h_kind) std::memcpy(h_kind, m->site_kind.data(), sizeof(int32_t) * m->site_kind.size());
+    return P2M_OK;
+}
+
+int p2m_get_lists(const p2m_index* h, int mesh, int64_t* h_offsets, int32_t* h_tri_ids) {
+    MeshData* m;
+    P2M_TRY(mesh_of(h, mesh, &m));
+    const int64_t S = (int64_t)m->site_kind.size();
+    std::vector<int32_t> off(S + 1);
+    if (S > 0 && m->d_row_off.p)
+        P2M_CUDA_TRY(cudaMemcpy(off.data(), m->d_row_off.p, sizeof(int32_t) * (S + 1), cudaMemcpyDeviceToHost));
+    if (h_offsets)
+        for (int64_t i = 0; i <= S; ++i) h_offsets[i] = off[i];
+    if (h_tri_ids && m->nnz > 0)
+        P2M_CUDA_TRY(cudaMemcpy(h_tri_ids, m->d_row_tri.p, sizeof(int32_t) * m->nnz, cudaMemcpyDeviceToHost));
+    return P2M_OK;
+}
+
+int p2m_get_balls(const p2m_index* h, int mesh, int64_t* h_ball_offsets, double* h_centres, double* h_radii) {
+    MeshData* m;
+    P2M_TRY(mesh_of(h, mesh, &m));
+    if (h_ball_offsets) std::memcpy(h_ball_offsets, m->ball_off.data(), sizeof(int64_t) * m->ball_off.size());
+    if (h_centres) std::memcpy(h_centres, m->ball_c.data(), sizeof(double) * m->ball_c.size());
+    if (h_radii) std::memcpy(h_radii, m->ball_r.data(), sizeof(double) * m->ball_r.size());
+    return P2M_OK;
+}
+
+}  // extern "C"
+
+// ----------------------------------------------------------------------------- not yet built
+extern "C" {
+int p2m_query_host(p2m_index*, const float*, int64_t, float*, float*, int32_t*, float*, void*) {
+    return fail(P2M_ERR_NOT_IMPLEMENTED, "p2m_query_host");
+}
+int p2m_backward(p2m_index*, const float*, int64_t, const int32_t*, const float*, const float*, float*, float*, void*) {
+    return fail(P2M_ERR_NOT_IMPLEMENTED, "p2m_backward");
+}
+int p2m_update_vertices(p2m_index*, const float*, void*) { return fail(P2M_ERR_NOT_IMPLEMENTED, "p2m_update_vertices"); }
+int p2m_batch_build(int, const float* const*, const int64_t*, const int32_t* const*, const int64_t*,
+                    const p2m_build_params*, void*, p2m_index** out) {
+    if (out) *out = nullptr;
+    return fail(P2M_ERR_NOT_IMPLEMENTED, "p2m_batch_build");
+}
+int p2m_batch_query(p2m_index*, const float*, const int64_t*, float*, float*, int32_t*, float*, int, int, void*) {
+    return fail(P2M_ERR_NOT_IMPLEMENTED, "p2m_batch_query");
+}
+}

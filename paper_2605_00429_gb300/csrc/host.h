@@ -1,0 +1,38 @@
+// Declarations that cross translation units between the C ABI and the build / query code.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "p2m_internal.h"
+
+struct p2m_index;
+
+namespace p2m {
+
+// State of the batched persistent query (tile queue, autotuned choice, captured graph).
+struct BatchState {
+    DevBuf views;        // MeshView per mesh (device copy)
+    DevBuf tiles;        // int4 work list: (mesh, q_begin, q_end, 0)
+    DevBuf counter;      // tile queue head
+    int n_tiles = 0;
+    int tile = 0;        // queries per tile picked by the autotuner
+    int schedule = 0;    // 1 thread / 2 warp per query
+    std::vector<int64_t> offsets;  // host offsets the work list was built for
+    const void* graph_pts = nullptr;
+    const void* graph_out[4] = {nullptr, nullptr, nullptr, nullptr};
+    cudaGraphExec_t exec = nullptr;
+    ~BatchState() { if (exec) cudaGraphExecDestroy(exec); }
+};
+
+unsigned* index_status(p2m_index* h);
+int check_status_word(p2m_index* h, cudaStream_t s, const char* what);
+
+// Sites, Delaunay, augmentation, corner balls, interception lists, nearest-site grid.
+int build_partition(MeshData& m, const p2m_build_params& prm, p2m_index* h, cudaStream_t s);
+
+// Full query of one mesh; counters (8 x u64, may be NULL) accumulate instrumentation.
+int run_query(p2m_index* h, MeshData& m, const float* d_pts, int64_t n, float* d_dist, float* d_closest,
+              int32_t* d_tri, float* d_bary, unsigned long long* counters, cudaStream_t s);
+int run_nearest_site(p2m_index* h, MeshData& m, const float* d_pts, int64_t n, int32_t* d_site, cudaStream_t s);
+
+}  // namespace p2m

@@ -1,0 +1,139 @@
+// Internal declarations shared by the translation units of libp2mpp.so.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/p2mpp.h"
+
+namespace p2m {
+
+// ----------------------------------------------------------------------------- errors
+
+void set_error(const std::string& msg);
+int fail(int code, const std::string& msg);
+
+#define P2M_CUDA_TRY(expr)                                                              \
+    do {                                                                                \
+        cudaError_t _e = (expr);                                                        \
+        if (_e != cudaSuccess)                                                          \
+            return ::p2m::fail(P2M_ERR_CUDA, std::string(#expr) + ": " +               \
+                                                 cudaGetErrorString(_e));               \
+    } while (0)
+
+#define P2M_TRY(expr)                  \
+    do {                               \
+        int _rc = (expr);              \
+        if (_rc != P2M_OK) return _rc; \
+    } while (0)
+
+// Device status word bits (written by kernels, read by the host after a sync).
+enum : unsigned {
+    ST_STACK = 1u,   // a BVH traversal stack overflowed
+    ST_LIMIT = 2u,   // an iteration / capacity cap was reached
+    ST_BAD = 4u,     // an index check failed
+};
+
+// ----------------------------------------------------------------------------- device buffers
+
+struct DevBuf {
+    void* p = nullptr;
+    size_t bytes = 0;
+    DevBuf() = default;
+    DevBuf(const DevBuf&) = delete;
+    DevBuf& operator=(const DevBuf&) = delete;
+    DevBuf(DevBuf&& o) noexcept : p(o.p), bytes(o.bytes) { o.p = nullptr; o.bytes = 0; }
+    DevBuf& operator=(DevBuf&& o) noexcept {
+        if (this != &o) { release(); p = o.p; bytes = o.bytes; o.p = nullptr; o.bytes = 0; }
+        return *this;
+    }
+    ~DevBuf() { release(); }
+    void release() { if (p) cudaFree(p); p = nullptr; bytes = 0; }
+    int alloc(size_t nbytes);          // (re)allocate, contents undefined
+    int ensure(size_t nbytes);         // grow if smaller
+    template <class T> T* as() const { return static_cast<T*>(p); }
+};
+
+// ----------------------------------------------------------------------------- BVH
+
+// Binary BVH node holding the boxes of both children (one 64-byte load tests both).
+// lo0.w / lo1.w carry the child references as int bits: >= 0 internal node, < 0 leaf ~prim.
+struct BNode {
+    float4 lo0, hi0, lo1, hi1;
+};
+
+struct Bvh {
+    DevBuf nodes;      // BNode[n-1]
+    int n_prims = 0;
+    int root = 0;      // node index, or ~prim when n_prims == 1
+};
+
+// ----------------------------------------------------------------------------- one mesh
+
+// Everything the query path of one mesh reads, as raw device pointers (for kernels).
+struct MeshView {
+    const float4* tri;      // [T][4] triangle records (see geom.cuh)
+    const float4* tsph;     // [T] bounding spheres (c.xyz, r)
+    const BNode* bvh;       // triangle BVH
+    int bvh_root;
+    const float4* sites;    // [S] (x, y, z, 0)
+    const int32_t* row_off; // [S+1]
+    const int32_t* row_tri; // [nnz]
+    const int32_t* cell_off;// [G^3+1] nearest-site grid CSR
+    const int32_t* cell_site;
+    int G;                  // grid cells per axis (0 => no grid: every query takes the BVH path)
+    float3 lo;              // domain D lower corner
+    float3 inv_h;           // 1 / grid cell size
+    float3 hi;              // domain D upper corner
+    float prune_abs;        // absolute prune slack
+    int n_tris;
+    int n_sites;
+};
+
+struct MeshData {
+    // host copies
+    std::vector<float> verts;    // [V*3]
+    std::vector<int32_t> tris;   // [T*3]
+    int64_t n_verts = 0, n_tris = 0;
+    double bb_lo[3], bb_hi[3], diag = 0;
+    double dom_lo[3], dom_hi[3];
+    // sites (host)
+    std::vector<float> site_pos;      // [S*3] float positions used by the queries
+    std::vector<double> site_ref;     // [S*3] reference point on the mesh
+    std::vector<int32_t> site_kind;   // 0 vertex site, 1 aux site
+    std::vector<int64_t> ball_off;    // [S+1]
+    std::vector<double> ball_c;       // [B*3]
+    std::vector<double> ball_r;       // [B]
+    // device
+    DevBuf d_verts, d_tris, d_tri, d_tsph;
+    Bvh bvh;
+    DevBuf d_sites, d_row_off, d_row_tri, d_cell_off, d_cell_site;
+    int64_t nnz = 0;
+    int G = 0;
+    float3 g_lo{}, g_hi{}, g_inv_h{};
+    p2m_stats stats{};
+    MeshView view() const;
+};
+
+// ----------------------------------------------------------------------------- kernels (launchers)
+
+// K0b: triangle records + bounding spheres.
+int launch_tri_precompute(const float* d_verts, const int32_t* d_tris, int n_tris, float4* d_tri,
+                          float4* d_tsph, cudaStream_t s);
+// K0: LBVH over primitive boxes (lo[i], hi[i]); scene centroid bounds given.
+int build_lbvh(const float4* d_lo, const float4* d_hi, int n, float3 c_lo, float3 c_hi, Bvh& out,
+               cudaStream_t s);
+int tri_boxes(const float* d_verts, const int32_t* d_tris, int n_tris, float4* lo, float4* hi,
+              cudaStream_t s);
+// K5: exact closest triangle by BVH branch and bound for a list of queries (idx may be NULL).
+int launch_bvh_closest(const MeshView& m, const float* d_pts, const int32_t* d_idx, int64_t n,
+                       float* d_dist, float* d_closest, int32_t* d_tri, float* d_bary,
+                       unsigned* d_status, cudaStream_t s);
+
+unsigned* status_word();  // device status word (process-wide, zero-initialised)
+int check_status(cudaStream_t s, const char* what);
+
+}  // namespace p2m

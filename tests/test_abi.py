@@ -1,0 +1,59 @@
+"""CPU checks of the boundary: the library builds, loads and exports every entry point that
+include/p2mpp.h declares (no compute calls: no GPU here)."""
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _declared():
+    src = open(os.path.join(ROOT, "include", "p2mpp.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(p2m_[a-z_]+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_2605_00429_gb300 import build as b
+    try:
+        b.build()
+    except RuntimeError as e:  # pragma: no cover - nvcc missing
+        pytest.skip(str(e))
+    import paper_2605_00429_gb300 as p
+    return p.lib()
+
+
+def test_header_parses():
+    names = _declared()
+    assert "p2m_build" in names and "p2m_query" in names and "p2m_backward" in names
+    assert len(names) >= 18
+
+
+def test_every_declared_symbol_is_exported(lib):
+    import paper_2605_00429_gb300 as p
+    for name in _declared():
+        assert hasattr(lib, name), name
+        assert name in p.SIGNATURES, f"binding lacks a signature for {name}"
+
+
+def test_defaults_and_errors_without_gpu(lib):
+    import ctypes
+    import paper_2605_00429_gb300 as p
+    prm = p.default_params()
+    assert abs(prm.domain_scale - 1.5) < 1e-7 and prm.enable_aux == 1 and prm.ring_sites == 12
+    assert lib.p2m_default_params(None) == -1
+    assert b"NULL" in lib.p2m_last_error()
+    assert lib.p2m_version().startswith(b"p2mpp")
+    lib.p2m_destroy(None)  # no-op
+
+
+def test_no_oracle_in_product():
+    """The product package never imports or loads the oracle."""
+    pkg = os.path.join(ROOT, "paper_2605_00429_gb300")
+    for dp, _, fs in os.walk(pkg):
+        for f in fs:
+            if f.endswith((".py", ".cu", ".cuh", ".cpp", ".h")):
+                txt = open(os.path.join(dp, f), errors="replace").read()
+                assert "import oracle" not in txt and "from oracle" not in txt and "_oracle.so" not in txt, f
