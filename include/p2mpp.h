@@ -41,7 +41,7 @@ extern "C" {
 #define P2M_ERR_CUDA (-2)            /* a CUDA runtime call failed */
 #define P2M_ERR_OOM (-3)             /* device or host allocation failed */
 #define P2M_ERR_EMPTY_MESH (-4)      /* no triangle, or no referenced vertex */
-#define P2M_ERR_DEGENERATE (-5)      /* fewer than 4 distinct sites, or all sites coplanar */
+#define P2M_ERR_DEGENERATE (-5)      /* all referenced vertices coincide */
 #define P2M_ERR_LIMIT (-6)           /* a device work cap or iteration cap was reached */
 #define P2M_ERR_STACK (-7)           /* a device BVH traversal stack overflowed */
 #define P2M_ERR_NOT_IMPLEMENTED (-8)
@@ -127,9 +127,11 @@ int p2m_default_params(p2m_build_params* out);
  *   verts[n_verts*3] float32, tris[n_tris*3] int32 (0-based).  If inputs_on_device != 0
  *   both are device pointers, else host pointers.  The mesh is copied; the caller may free
  *   its arrays when the call returns.  params may be NULL (defaults).
+ * A mesh with fewer than 4 distinct vertices gets no site partition: its queries all take
+ * the exact BVH search (same results, no localisation).
  * Synchronises `stream`.  On success *out owns the index (release with p2m_destroy).
  * Errors: INVALID_ARG (NULL, NaN/Inf vertex, index out of range, n <= 0), EMPTY_MESH,
- * DEGENERATE, OOM, CUDA, STACK, LIMIT. */
+ * DEGENERATE, OOM, CUDA, STACK, LIMIT (lists beyond 2^31 entries). */
 int p2m_build(const float* verts, int64_t n_verts, const int32_t* tris, int64_t n_tris,
               int inputs_on_device, const p2m_build_params* params, void* stream,
               p2m_index** out);
@@ -226,6 +228,19 @@ int p2m_get_lists(const p2m_index* h, int mesh, int64_t* h_offsets, int32_t* h_t
  * h_centres[n_balls*3] (float64) and h_radii[n_balls] (float64, before slack). */
 int p2m_get_balls(const p2m_index* h, int mesh, int64_t* h_ball_offsets, double* h_centres,
                   double* h_radii);
+
+/* ---- Host-only stage (no GPU needed). ------------------------------------------------ */
+
+/* The clipped Voronoi cells of a point set exactly as p2m_build computes them (Section 3.3:
+ * the cells whose corners carry the balls of Eq. 3): each site is moved to the library's
+ * lattice (at most about 2e-6 of the domain size away; the moved positions are returned in
+ * h_sites_out[n*3]), the exact Delaunay triangulation gives each site's neighbours, and the
+ * box D = [dom_lo, dom_hi] is cut by the neighbours' bisector planes in FP64.
+ *   h_sites[n*3] float32 inside D, n >= 4.  Outputs h_corner_off[n+1] (CSR over sites) and
+ *   h_corners[n_corners*3] (FP64); call once with h_corners == NULL to learn *n_corners.
+ * Errors: INVALID_ARG (NULL, n < 4, a site outside D), INTERNAL. */
+int p2m_voronoi_cells(const float* h_sites, int64_t n, const double* dom_lo, const double* dom_hi, int seed,
+                      float* h_sites_out, int64_t* h_corner_off, double* h_corners, int64_t* n_corners);
 
 #ifdef __cplusplus
 }

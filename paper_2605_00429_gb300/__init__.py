@@ -81,6 +81,7 @@ SIGNATURES = {
     "p2m_get_sites": ([_P, _I, _P, _P, _P], _I),
     "p2m_get_lists": ([_P, _I, _P, _P], _I),
     "p2m_get_balls": ([_P, _I, _P, _P, _P], _I),
+    "p2m_voronoi_cells": ([_P, _I64, _P, _P, _I, _P, _P, _P, _P], _I),
 }
 
 
@@ -284,6 +285,25 @@ class P2MIndex:
         _check(lib().p2m_get_balls(self._h, mesh, off.ctypes.data_as(_P), c.ctypes.data_as(_P),
                                    r.ctypes.data_as(_P)))
         return off, c[:B], r[:B]
+
+
+def voronoi_cells(sites, dom_lo, dom_hi, seed=1):
+    """Host-only: the clipped Voronoi cells the build computes.  Returns (moved sites [n,3]
+    float32, corner offsets [n+1], corners [m,3] float64)."""
+    s = np.ascontiguousarray(np.asarray(sites, dtype=np.float32).reshape(-1, 3))
+    lo = np.ascontiguousarray(np.asarray(dom_lo, dtype=np.float64))
+    hi = np.ascontiguousarray(np.asarray(dom_hi, dtype=np.float64))
+    n = s.shape[0]
+    cnt = ctypes.c_int64()
+    _check(lib().p2m_voronoi_cells(s.ctypes.data_as(_P), n, lo.ctypes.data_as(_P), hi.ctypes.data_as(_P), seed,
+                                   None, None, None, ctypes.byref(cnt)))
+    moved = np.empty((n, 3), np.float32)
+    off = np.empty(n + 1, np.int64)
+    cor = np.empty((max(cnt.value, 1), 3), np.float64)
+    _check(lib().p2m_voronoi_cells(s.ctypes.data_as(_P), n, lo.ctypes.data_as(_P), hi.ctypes.data_as(_P), seed,
+                                   moved.ctypes.data_as(_P), off.ctypes.data_as(_P), cor.ctypes.data_as(_P),
+                                   ctypes.byref(cnt)))
+    return moved, off, cor[:cnt.value]
 
 
 def _make_function():

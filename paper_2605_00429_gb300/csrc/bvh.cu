@@ -299,11 +299,11 @@ __device__ __forceinline__ unsigned long long bvh_closest_key(float3 q, const BN
 }
 
 __global__ void k_bvh_closest(const BNode* __restrict__ nodes, int root, const float4* __restrict__ tri,
-                              const float* __restrict__ pts, const int32_t* __restrict__ idx, int64_t n,
-                              float* __restrict__ dist, float* __restrict__ closest, int32_t* __restrict__ tri_out,
-                              float* __restrict__ bary, unsigned* status) {
-    const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (k >= n) return;
+                              const float* __restrict__ pts, const int32_t* __restrict__ idx, const int* __restrict__ count,
+                              int64_t n, float* __restrict__ dist, float* __restrict__ closest,
+                              int32_t* __restrict__ tri_out, float* __restrict__ bary, unsigned* status) {
+    const int64_t nn = count ? (int64_t)*count : n;
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nn; k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = idx ? idx[k] : k;
     const float3 q = make_float3(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]);
     float s = 0.0f, t = 0.0f;
@@ -318,14 +318,20 @@ __global__ void k_bvh_closest(const BNode* __restrict__ nodes, int root, const f
         closest[3 * i] = p.x; closest[3 * i + 1] = p.y; closest[3 * i + 2] = p.z;
     }
     if (bary) { bary[3 * i] = 1.0f - s - t; bary[3 * i + 1] = s; bary[3 * i + 2] = t; }
+    }
 }
 
-int launch_bvh_closest(const MeshView& m, const float* d_pts, const int32_t* d_idx, int64_t n, float* d_dist,
-                       float* d_closest, int32_t* d_tri, float* d_bary, unsigned* d_status, cudaStream_t s) {
+int launch_bvh_closest(const MeshView& m, const float* d_pts, const int32_t* d_idx, const int* d_count, int64_t n,
+                       float* d_dist, float* d_closest, int32_t* d_tri, float* d_bary, unsigned* d_status,
+                       cudaStream_t s) {
     if (n <= 0) return P2M_OK;
     const int bs = 128;
-    k_bvh_closest<<<(unsigned)((n + bs - 1) / bs), bs, 0, s>>>(m.bvh, m.bvh_root, m.tri, d_pts, d_idx, n, d_dist,
-                                                              d_closest, d_tri, d_bary, d_status);
+    // with a device-side count the launch is sized for a modest share of n: the grid-stride
+    // loop covers the rest
+    const int64_t want = (n + bs - 1) / bs;
+    const int64_t blocks = d_count ? std::min<int64_t>(want, 152 * 8) : std::min<int64_t>(want, 152 * 64);
+    k_bvh_closest<<<(unsigned)std::max<int64_t>(blocks, 1), bs, 0, s>>>(m.bvh, m.bvh_root, m.tri, d_pts, d_idx, d_count,
+                                                                         n, d_dist, d_closest, d_tri, d_bary, d_status);
     P2M_CUDA_TRY(cudaGetLastError());
     return P2M_OK;
 }

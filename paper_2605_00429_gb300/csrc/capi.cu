@@ -48,6 +48,7 @@ MeshView MeshData::view() const {
     v.bvh = bvh.nodes.as<const BNode>();
     v.bvh_root = bvh.root;
     v.sites = d_sites.as<const float4>();
+    v.refs = d_refs.as<const float4>();
     v.row_off = d_row_off.as<const int32_t>();
     v.row_tri = d_row_tri.as<const int32_t>();
     v.cell_off = d_cell_off.as<const int32_t>();
@@ -84,6 +85,7 @@ struct p2m_index {
 namespace p2m {
 
 unsigned* index_status(p2m_index* h) { return h->status.as<unsigned>(); }
+DevBuf& index_rest(p2m_index* h) { return h->scratch_idx; }
 
 int check_status_word(p2m_index* h, cudaStream_t s, const char* what) {
     unsigned st = 0;

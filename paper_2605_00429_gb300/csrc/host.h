@@ -25,6 +25,7 @@ struct BatchState {
 };
 
 unsigned* index_status(p2m_index* h);
+DevBuf& index_rest(p2m_index* h);  // scratch for the compacted out-of-domain query list
 int check_status_word(p2m_index* h, cudaStream_t s, const char* what);
 
 // Sites, Delaunay, augmentation, corner balls, interception lists, nearest-site grid.

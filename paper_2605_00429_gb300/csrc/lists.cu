@@ -1,0 +1,162 @@
+// K1: interception lists by corner-sphere vs BVH collision (Section 3.3 "Implementation
+// Details").  The list of site v holds every triangle f that meets the union of its balls:
+//   vertex site:  balls B(u, ||u - v||) over the corners u of its clipped cell (Eq. 3);
+//   aux site:     one ball B(s, r) with r from Eq. 8.
+// Ball centres and radii arrive in FP32 with the radius already inflated on the host by the
+// build slack plus the FP32 rounding of the centre, so a triangle whose FP64 distance to a
+// ball is <= r joins the list (the test is solid ball vs solid triangle).
+//
+// One warp per site; lanes split the site's balls.  The warp walks the BVH in lockstep
+// (the traversal stack is warp-uniform); a node is entered if any lane's ball overlaps the
+// node box, a triangle is kept if any lane's ball reaches it.  Two passes share the code:
+// count, then (after a scan) fill.  Both passes visit triangles in the same order.
+#include <cub/device/device_scan.cuh>
+
+#include "geom.cuh"
+#include "host.h"
+
+namespace p2m {
+
+constexpr int kListWarps = 4;     // warps per block
+constexpr int kListStack = 64;
+
+__device__ __forceinline__ bool any_ball_box(const float4* __restrict__ balls, int nb, float3 lo, float3 hi) {
+    bool hit = false;
+    for (int k = threadIdx.x & 31; k < nb && !hit; k += 32) {
+        const float4 b = __ldg(balls + k);
+        hit = box_dist2(f3(b), lo, hi) <= b.w * b.w;
+    }
+    return __any_sync(0xffffffffu, hit);
+}
+
+__device__ __forceinline__ bool any_ball_tri(const float4* __restrict__ balls, int nb, const TriRec& T) {
+    bool hit = false;
+    for (int k = threadIdx.x & 31; k < nb && !hit; k += 32) {
+        const float4 b = __ldg(balls + k);
+        float s, t;
+        hit = tri_dist2(f3(b), T, s, t) <= b.w * b.w;
+    }
+    return __any_sync(0xffffffffu, hit);
+}
+
+template <bool FILL>
+__global__ void __launch_bounds__(32 * kListWarps) k_lists(const float4* __restrict__ balls, const int64_t* __restrict__ ball_off,
+                                                            int n_sites, const BNode* __restrict__ nodes, int root,
+                                                            const float4* __restrict__ tri, int64_t* __restrict__ count,
+                                                            const int64_t* __restrict__ row_off64, int32_t* __restrict__ row_tri,
+                                                            unsigned* status) {
+    __shared__ int stk[kListWarps][kListStack];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int nwarps = gridDim.x * kListWarps;
+    for (int s = blockIdx.x * kListWarps + w; s < n_sites; s += nwarps) {
+        const int64_t b0 = ball_off[s];
+        const int nb = (int)(ball_off[s + 1] - b0);
+        const float4* sb = balls + b0;
+        int64_t k = 0;
+        int64_t out = FILL ? row_off64[s] : 0;
+        auto emit = [&](int f) {
+            if (FILL && lane == 0) row_tri[out + k] = f;
+            ++k;
+        };
+        if (nb > 0) {
+            if (root < 0) {
+                const TriRec T = load_tri(tri, ~root);
+                if (any_ball_tri(sb, nb, T)) emit(~root);
+            } else {
+                int sp = 0;
+                int node = root;
+                while (node >= 0) {
+                    const float4* np = reinterpret_cast<const float4*>(nodes + node);
+                    const float4 lo0 = __ldg(np), hi0 = __ldg(np + 1), lo1 = __ldg(np + 2), hi1 = __ldg(np + 3);
+                    const int c0 = __float_as_int(lo0.w), c1 = __float_as_int(lo1.w);
+                    const bool h0 = any_ball_box(sb, nb, f3(lo0), f3(hi0));
+                    const bool h1 = any_ball_box(sb, nb, f3(lo1), f3(hi1));
+                    int next = -1;
+                    if (h0) {
+                        if (c0 < 0) {
+                            const TriRec T = load_tri(tri, ~c0);
+                            if (any_ball_tri(sb, nb, T)) emit(~c0);
+                        } else {
+                            next = c0;
+                        }
+                    }
+                    if (h1) {
+                        if (c1 < 0) {
+                            const TriRec T = load_tri(tri, ~c1);
+                            if (any_ball_tri(sb, nb, T)) emit(~c1);
+                        } else if (next < 0) {
+                            next = c1;
+                        } else {
+                            if (sp < kListStack) {
+                                if (lane == 0) stk[w][sp] = c1;
+                                ++sp;
+                            } else if (lane == 0) {
+                                atomicOr(status, ST_STACK);
+                            }
+                        }
+                    }
+                    __syncwarp();
+                    if (next < 0) {
+                        if (sp > 0) {
+                            --sp;
+                            next = stk[w][sp];
+                        }
+                    }
+                    __syncwarp();
+                    node = next;
+                }
+            }
+        }
+        if (!FILL && lane == 0) count[s] = k;
+        if (FILL && lane == 0 && k != row_off64[s + 1] - row_off64[s]) atomicOr(status, ST_BAD);
+    }
+}
+
+__global__ void k_i64_to_i32(const int64_t* __restrict__ a, int32_t* __restrict__ b, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        b[i] = (int32_t)a[i];
+}
+
+// Builds m.d_row_off / m.d_row_tri from the device ball table (d_balls, d_ball_off).
+int build_lists(MeshData& m, const float4* d_balls, const int64_t* d_ball_off, int n_sites, unsigned* status,
+                cudaStream_t s) {
+    DevBuf cnt, off64, tmp;
+    P2M_TRY(cnt.alloc(sizeof(int64_t) * (n_sites + 1)));
+    P2M_TRY(off64.alloc(sizeof(int64_t) * (n_sites + 1)));
+    const int blocks = std::max(1, std::min((n_sites + kListWarps - 1) / kListWarps, 152 * 16));
+    const MeshView v = m.view();
+    k_lists<false><<<blocks, 32 * kListWarps, 0, s>>>(d_balls, d_ball_off, n_sites, v.bvh, v.bvh_root, v.tri,
+                                                     cnt.as<int64_t>(), nullptr, nullptr, status);
+    P2M_CUDA_TRY(cudaGetLastError());
+    P2M_CUDA_TRY(cudaMemsetAsync(cnt.as<int64_t>() + n_sites, 0, sizeof(int64_t), s));
+    size_t tb = 0;
+    P2M_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, tb, cnt.as<int64_t>(), off64.as<int64_t>(), n_sites + 1, s));
+    P2M_TRY(tmp.alloc(tb + 16));
+    P2M_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp.p, tb, cnt.as<int64_t>(), off64.as<int64_t>(), n_sites + 1, s));
+    int64_t nnz = 0;
+    P2M_CUDA_TRY(cudaMemcpyAsync(&nnz, off64.as<int64_t>() + n_sites, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    P2M_CUDA_TRY(cudaStreamSynchronize(s));
+    if (nnz > 0x7fffffffLL)
+        return fail(P2M_ERR_LIMIT, "interception lists hold " + std::to_string(nnz) +
+                                       " entries (> 2^31); enable site augmentation or coarsen the mesh");
+    m.nnz = nnz;
+    P2M_TRY(m.d_row_tri.alloc(sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
+    P2M_TRY(m.d_row_off.alloc(sizeof(int32_t) * (n_sites + 1)));
+    k_lists<true><<<blocks, 32 * kListWarps, 0, s>>>(d_balls, d_ball_off, n_sites, v.bvh, v.bvh_root, v.tri, nullptr,
+                                                    off64.as<int64_t>(), m.d_row_tri.as<int32_t>(), status);
+    P2M_CUDA_TRY(cudaGetLastError());
+    k_i64_to_i32<<<64, 256, 0, s>>>(off64.as<int64_t>(), m.d_row_off.as<int32_t>(), n_sites + 1);
+    P2M_CUDA_TRY(cudaGetLastError());
+    // row statistics (Table 1 Max / Avg)
+    std::vector<int64_t> c(n_sites);
+    P2M_CUDA_TRY(cudaMemcpyAsync(c.data(), cnt.p, sizeof(int64_t) * n_sites, cudaMemcpyDeviceToHost, s));
+    P2M_CUDA_TRY(cudaStreamSynchronize(s));
+    int64_t mx = 0;
+    for (int64_t x : c) mx = std::max(mx, x);
+    m.stats.nnz = nnz;
+    m.stats.max_row = mx;
+    m.stats.avg_row = n_sites ? (double)nnz / n_sites : 0.0;
+    return P2M_OK;
+}
+
+}  // namespace p2m

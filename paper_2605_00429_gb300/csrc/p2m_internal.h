@@ -80,6 +80,7 @@ struct MeshView {
     const BNode* bvh;       // triangle BVH
     int bvh_root;
     const float4* sites;    // [S] (x, y, z, 0)
+    const float4* refs;     // [S] reference point on the mesh (x, y, z, rounding radius)
     const int32_t* row_off; // [S+1]
     const int32_t* row_tri; // [nnz]
     const int32_t* cell_off;// [G^3+1] nearest-site grid CSR
@@ -110,7 +111,7 @@ struct MeshData {
     // device
     DevBuf d_verts, d_tris, d_tri, d_tsph;
     Bvh bvh;
-    DevBuf d_sites, d_row_off, d_row_tri, d_cell_off, d_cell_site;
+    DevBuf d_sites, d_refs, d_row_off, d_row_tri, d_cell_off, d_cell_site;
     int64_t nnz = 0;
     int G = 0;
     float3 g_lo{}, g_hi{}, g_inv_h{};
@@ -128,12 +129,11 @@ int build_lbvh(const float4* d_lo, const float4* d_hi, int n, float3 c_lo, float
                cudaStream_t s);
 int tri_boxes(const float* d_verts, const int32_t* d_tris, int n_tris, float4* lo, float4* hi,
               cudaStream_t s);
-// K5: exact closest triangle by BVH branch and bound for a list of queries (idx may be NULL).
-int launch_bvh_closest(const MeshView& m, const float* d_pts, const int32_t* d_idx, int64_t n,
-                       float* d_dist, float* d_closest, int32_t* d_tri, float* d_bary,
+// K5: exact closest triangle by BVH branch and bound.  Queries are d_pts[d_idx[k]] for
+// k < *d_count (both on the device) when d_idx is given, else d_pts[k] for k < n.  n bounds
+// the launch either way.
+int launch_bvh_closest(const MeshView& m, const float* d_pts, const int32_t* d_idx, const int* d_count,
+                       int64_t n, float* d_dist, float* d_closest, int32_t* d_tri, float* d_bary,
                        unsigned* d_status, cudaStream_t s);
-
-unsigned* status_word();  // device status word (process-wide, zero-initialised)
-int check_status(cudaStream_t s, const char* what);
 
 }  // namespace p2m

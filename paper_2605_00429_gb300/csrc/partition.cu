@@ -1,12 +1,488 @@
-// Build of the site partition and of everything the query reads besides the triangles.
+// Build of the site partition and of everything the query reads besides the triangles:
+//   sites (Section 3.1: mesh vertices as proxy sites), their exact Delaunay triangulation,
+//   ring-based augmentation (Section 3.2), clipped Voronoi cells, the corner balls of Eq. 3
+//   and Eq. 8, the interception lists (K1, lists.cu) and the nearest-site grid (K2a,
+//   grid.cu).
+#include <algorithm>
+#include <array>
+#include <chrono>
+#include <cmath>
+#include <cstring>
+#include <unordered_map>
+
 #include "host.h"
+#include "host_geom.h"
+#include "voronoi.h"
 
 namespace p2m {
 
+int build_lists(MeshData& m, const float4* d_balls, const int64_t* d_ball_off, int n_sites, unsigned* status,
+                cudaStream_t s);
+int build_grid(MeshData& m, const Bvh& site_bvh, int G, unsigned* status, cudaStream_t s);
+
+static double ms_now() {
+    using namespace std::chrono;
+    return duration<double, std::milli>(steady_clock::now().time_since_epoch()).count();
+}
+
+static inline uint64_t mix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+// FP64 closest point of a triangle (host; the same parametrisation as the device routine).
+static void closest_on_tri_f64(const double q[3], const double a[3], const double b[3], const double c[3], double p[3]) {
+    double e0[3], e1[3], w[3], n[3];
+    for (int k = 0; k < 3; ++k) { e0[k] = b[k] - a[k]; e1[k] = c[k] - a[k]; w[k] = q[k] - a[k]; }
+    n[0] = e0[1] * e1[2] - e0[2] * e1[1]; n[1] = e0[2] * e1[0] - e0[0] * e1[2]; n[2] = e0[0] * e1[1] - e0[1] * e1[0];
+    const double nn = n[0] * n[0] + n[1] * n[1] + n[2] * n[2];
+    auto dot = [](const double* x, const double* y) { return x[0] * y[0] + x[1] * y[1] + x[2] * y[2]; };
+    if (nn > 0) {
+        double wx1[3] = {w[1] * e1[2] - w[2] * e1[1], w[2] * e1[0] - w[0] * e1[2], w[0] * e1[1] - w[1] * e1[0]};
+        double e0xw[3] = {e0[1] * w[2] - e0[2] * w[1], e0[2] * w[0] - e0[0] * w[2], e0[0] * w[1] - e0[1] * w[0]};
+        const double s = dot(wx1, n) / nn, t = dot(e0xw, n) / nn;
+        if (s >= 0 && t >= 0 && s + t <= 1) {
+            for (int k = 0; k < 3; ++k) p[k] = a[k] + s * e0[k] + t * e1[k];
+            return;
+        }
+    }
+    const double* A[3] = {a, a, b};
+    const double* B[3] = {b, c, c};
+    double best = 1e300;
+    for (int e = 0; e < 3; ++e) {
+        double d[3], r[3];
+        for (int k = 0; k < 3; ++k) { d[k] = B[e][k] - A[e][k]; r[k] = q[k] - A[e][k]; }
+        const double l = dot(d, d);
+        double u = l > 0 ? dot(r, d) / l : 0.0;
+        u = std::min(1.0, std::max(0.0, u));
+        double x[3];
+        for (int k = 0; k < 3; ++k) x[k] = A[e][k] + u * d[k];
+        const double dd = (q[0] - x[0]) * (q[0] - x[0]) + (q[1] - x[1]) * (q[1] - x[1]) + (q[2] - x[2]) * (q[2] - x[2]);
+        if (dd < best) { best = dd; p[0] = x[0]; p[1] = x[1]; p[2] = x[2]; }
+    }
+}
+
+// Unit directions of the auxiliary ring: icosahedron (12) or octahedron (6) vertices.
+static std::vector<double> ring_dirs(int n) {
+    std::vector<double> d;
+    if (n == 6) {
+        d = {1, 0, 0, -1, 0, 0, 0, 1, 0, 0, -1, 0, 0, 0, 1, 0, 0, -1};
+        return d;
+    }
+    const double t = (1.0 + std::sqrt(5.0)) / 2.0, s = 1.0 / std::sqrt(1.0 + t * t);
+    const double v[12][3] = {{-1, t, 0}, {1, t, 0}, {-1, -t, 0}, {1, -t, 0}, {0, -1, t}, {0, 1, t},
+                             {0, -1, -t}, {0, 1, -t}, {t, 0, -1}, {t, 0, 1}, {-t, 0, -1}, {-t, 0, 1}};
+    for (auto& p : v)
+        for (int k = 0; k < 3; ++k) d.push_back(p[k] * s);
+    return d;
+}
+
+// Spatial hash of points for "is any point within r of x" checks on the host.
+struct PointHash {
+    double cell;
+    std::unordered_map<uint64_t, std::vector<int>> m;
+    std::vector<double> P;
+    static uint64_t key(int64_t x, int64_t y, int64_t z) {
+        return ((uint64_t)(x & 0x1fffff) << 42) | ((uint64_t)(y & 0x1fffff) << 21) | (uint64_t)(z & 0x1fffff);
+    }
+    void add(const double p[3]) {
+        const int id = (int)(P.size() / 3);
+        P.insert(P.end(), p, p + 3);
+        m[key((int64_t)std::floor(p[0] / cell), (int64_t)std::floor(p[1] / cell), (int64_t)std::floor(p[2] / cell))]
+            .push_back(id);
+    }
+    bool near(const double p[3], double r) const {
+        const int64_t cx = (int64_t)std::floor(p[0] / cell), cy = (int64_t)std::floor(p[1] / cell),
+                      cz = (int64_t)std::floor(p[2] / cell);
+        const int64_t k = (int64_t)std::ceil(r / cell);
+        for (int64_t dx = -k; dx <= k; ++dx)
+            for (int64_t dy = -k; dy <= k; ++dy)
+                for (int64_t dz = -k; dz <= k; ++dz) {
+                    auto it = m.find(key(cx + dx, cy + dy, cz + dz));
+                    if (it == m.end()) continue;
+                    for (int id : it->second) {
+                        const double* q = &P[3 * id];
+                        const double d2 = (q[0] - p[0]) * (q[0] - p[0]) + (q[1] - p[1]) * (q[1] - p[1]) + (q[2] - p[2]) * (q[2] - p[2]);
+                        if (d2 < r * r) return true;
+                    }
+                }
+        return false;
+    }
+};
+
+// Section 3.2: bin the Voronoi vertices into a tau-grid, flag dense cells, and add a centre
+// site plus a ring of auxiliary sites on an enclosing sphere for each; ring sites that fall
+// near an existing site or inside another flagged cell's bounding sphere are dropped.
+// Returns the number of auxiliary sites appended to ss.pts.
+static int augment(SiteSet& ss, const MeshData& m, const p2m_build_params& prm, int64_t& n_dense) {
+    n_dense = 0;
+    // tau from the mean edge length
+    double sum = 0;
+    int64_t ne = 0;
+    for (int64_t f = 0; f < m.n_tris; ++f)
+        for (int k = 0; k < 3; ++k) {
+            const float* a = &m.verts[3 * (int64_t)m.tris[3 * f + k]];
+            const float* b = &m.verts[3 * (int64_t)m.tris[3 * f + (k + 1) % 3]];
+            sum += std::sqrt((double)(a[0] - b[0]) * (a[0] - b[0]) + (double)(a[1] - b[1]) * (a[1] - b[1]) +
+                             (double)(a[2] - b[2]) * (a[2] - b[2]));
+            ++ne;
+        }
+    const double tau = prm.tau_scale * sum / std::max<int64_t>(ne, 1);
+    if (!(tau > 0)) return 0;
+    std::vector<double> cc;
+    ss.dt.circumcentres(cc);
+    std::unordered_map<uint64_t, int> count;
+    auto cell_of = [&](const double* x, int64_t* c) {
+        for (int k = 0; k < 3; ++k) c[k] = (int64_t)std::floor((x[k] - m.dom_lo[k]) / tau);
+    };
+    const int64_t nc = (int64_t)std::ceil((m.dom_hi[0] - m.dom_lo[0]) / tau) + 2;
+    auto key = [&](const int64_t* c) { return (uint64_t)((c[2] * nc + c[1]) * nc + c[0]); };
+    for (size_t i = 0; i + 2 < cc.size(); i += 3) {
+        double w[3];
+        for (int k = 0; k < 3; ++k) w[k] = (cc[i + k] + (double)ss.lat.c[k]) * ss.lat.h;
+        bool in = true;
+        for (int k = 0; k < 3; ++k) in &= w[k] >= m.dom_lo[k] && w[k] <= m.dom_hi[k];
+        if (!in) continue;
+        int64_t c[3];
+        cell_of(w, c);
+        count[key(c)]++;
+    }
+    if (count.empty()) return 0;
+    std::vector<int> vals;
+    for (auto& kv : count) vals.push_back(kv.second);
+    std::nth_element(vals.begin(), vals.begin() + vals.size() / 2, vals.end());
+    const double median = vals[vals.size() / 2];
+    const double thresh = std::max((double)prm.density_min, prm.density_factor * median);
+    std::vector<std::array<double, 3>> centres;
+    for (auto& kv : count) {
+        if (kv.second <= thresh) continue;
+        const uint64_t k = kv.first;
+        const int64_t cx = (int64_t)(k % nc), cy = (int64_t)((k / nc) % nc), cz = (int64_t)(k / ((uint64_t)nc * nc));
+        centres.push_back({m.dom_lo[0] + (cx + 0.5) * tau, m.dom_lo[1] + (cy + 0.5) * tau, m.dom_lo[2] + (cz + 0.5) * tau});
+    }
+    std::sort(centres.begin(), centres.end());
+    n_dense = (int64_t)centres.size();
+    if (centres.empty()) return 0;
+    PointHash sites;
+    sites.cell = std::max(tau, 1e-30);
+    for (int i = 0; i < (int)ss.pts.size(); ++i) {
+        double w[3];
+        ss.world(i, w);
+        sites.add(w);
+    }
+    PointHash flagged;
+    flagged.cell = tau;
+    for (auto& c : centres) flagged.add(c.data());
+    const double ring_r = prm.ring_radius_scale * tau;
+    const double bound_r = 0.5 * std::sqrt(3.0) * tau;  // a flagged cell's bounding sphere
+    const std::vector<double> dirs = ring_dirs(prm.ring_sites);
+    int added = 0;
+    auto try_add = [&](const double* p) {
+        bool in = true;
+        for (int k = 0; k < 3; ++k) in &= p[k] > m.dom_lo[k] && p[k] < m.dom_hi[k];
+        if (!in || sites.near(p, 0.5 * tau)) return;
+        const IPt q = ss.lat.to_lattice(p);
+        if (!ss.lat.inside(q)) return;
+        ss.pts.push_back(q);
+        sites.add(p);
+        ++added;
+    };
+    for (auto& c : centres) try_add(c.data());
+    for (auto& c : centres)
+        for (size_t d = 0; d < dirs.size(); d += 3) {
+            const double p[3] = {c[0] + ring_r * dirs[d], c[1] + ring_r * dirs[d + 1], c[2] + ring_r * dirs[d + 2]};
+            if (flagged.near(p, bound_r)) continue;  // merged ring of adjacent flagged cells
+            try_add(p);
+        }
+    return added;
+}
+
 int build_partition(MeshData& m, const p2m_build_params& prm, p2m_index* h, cudaStream_t s) {
-    (void)prm; (void)h; (void)s;
-    m.G = 0;  // no grid yet: every query takes the exact BVH search
+    p2m_stats& st = m.stats;
+    unsigned* status = index_status(h);
+    double t0 = ms_now();
+    SiteSet ss;
+    if (!ss.lat.setup(m.dom_lo, m.dom_hi)) return fail(P2M_ERR_DEGENERATE, "domain lattice setup failed");
+    // vertex sites: referenced vertices, merged when they share a lattice point
+    std::vector<char> used(m.n_verts, 0);
+    for (int64_t i = 0; i < m.n_tris * 3; ++i) used[m.tris[i]] = 1;
+    std::vector<std::pair<std::array<int64_t, 3>, int>> lv;
+    for (int64_t i = 0; i < m.n_verts; ++i) {
+        if (!used[i]) continue;
+        const double p[3] = {m.verts[3 * i], m.verts[3 * i + 1], m.verts[3 * i + 2]};
+        const IPt q = ss.lat.to_lattice(p);
+        lv.push_back({{q.x, q.y, q.z}, (int)i});
+    }
+    std::sort(lv.begin(), lv.end());
+    std::vector<int> ref_vertex;
+    uint64_t rng = mix64((uint64_t)prm.seed * 0x100000001b3ull + 17);
+    for (size_t i = 0; i < lv.size(); ++i) {
+        if (i > 0 && lv[i].first == lv[i - 1].first) continue;
+        IPt q{lv[i].first[0], lv[i].first[1], lv[i].first[2]};
+        // one lattice step of jitter breaks the exact co-planarity / co-sphericity of
+        // symmetric meshes; a site is only a partition generator, so any nearby point works
+        rng = mix64(rng);
+        q.x += (int64_t)(rng % 3) - 1;
+        q.y += (int64_t)((rng >> 8) % 3) - 1;
+        q.z += (int64_t)((rng >> 16) % 3) - 1;
+        ss.pts.push_back(q);
+        ref_vertex.push_back(lv[i].second);
+    }
+    const int n_vsites = (int)ss.pts.size();
+    if (n_vsites < 4) {
+        // too few sites for a 3D partition: every query takes the exact BVH search
+        m.G = 0;
+        return P2M_OK;
+    }
+    std::string err;
+    ss.dt.init(ss.lat.R);
+    if (ss.triangulate_from(0, (uint64_t)prm.seed, err)) return fail(P2M_ERR_INTERNAL, err);
+    if (ss.dt.count_real_tets() == 0) return fail(P2M_ERR_DEGENERATE, "all sites are coplanar");
+    double t1 = ms_now();
+    st.ms_delaunay = t1 - t0;
+    int n_aux = 0;
+    int64_t n_dense = 0;
+    if (prm.enable_aux) {
+        n_aux = augment(ss, m, prm, n_dense);
+        if (n_aux > 0 && ss.triangulate_from(n_vsites, (uint64_t)prm.seed + 1, err)) return fail(P2M_ERR_INTERNAL, err);
+    }
+    double t2 = ms_now();
+    st.ms_aug = t2 - t1;
+    st.n_dense_cells = n_dense;
+    st.n_delaunay_tets = ss.dt.count_real_tets();
+    ss.neighbour_csr();
+    if (ss.clip_cells(m.dom_lo, m.dom_hi, m.diag, hardware_threads()))
+        return fail(P2M_ERR_INTERNAL, "a Voronoi cell clipped to nothing");
+    double t3 = ms_now();
+    st.ms_cells = t3 - t2;
+    const int S = (int)ss.pts.size();
+    st.n_sites = S;
+    st.n_vertex_sites = n_vsites;
+    st.n_aux_sites = S - n_vsites;
+    // site positions (FP32-exact) and reference points
+    m.site_pos.resize(3 * S);
+    m.site_ref.resize(3 * S);
+    m.site_kind.assign(S, 0);
+    for (int i = 0; i < S; ++i) {
+        double w[3];
+        ss.world(i, w);
+        for (int k = 0; k < 3; ++k) m.site_pos[3 * i + k] = (float)w[k];
+        if (i < n_vsites) {
+            for (int k = 0; k < 3; ++k) m.site_ref[3 * i + k] = (double)m.verts[3 * (int64_t)ref_vertex[i] + k];
+        } else {
+            m.site_kind[i] = 1;
+        }
+    }
+    P2M_TRY(m.d_sites.alloc(sizeof(float4) * S));
+    {
+        std::vector<float4> sp(S);
+        for (int i = 0; i < S; ++i) sp[i] = make_float4(m.site_pos[3 * i], m.site_pos[3 * i + 1], m.site_pos[3 * i + 2], 0.f);
+        P2M_CUDA_TRY(cudaMemcpyAsync(m.d_sites.p, sp.data(), sizeof(float4) * S, cudaMemcpyHostToDevice, s));
+        P2M_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    // proj(s, M) of the auxiliary sites: exact BVH search on the device, then the closest
+    // point recomputed in FP64 on the winning triangle (so it lies on M)
+    if (S > n_vsites) {
+        const int na = S - n_vsites;
+        DevBuf dd, dt;
+        P2M_TRY(dd.alloc(sizeof(float) * na));
+        P2M_TRY(dt.alloc(sizeof(int32_t) * na));
+        DevBuf pts;
+        P2M_TRY(pts.alloc(sizeof(float) * 3 * na));
+        P2M_CUDA_TRY(cudaMemcpyAsync(pts.p, m.site_pos.data() + 3 * n_vsites, sizeof(float) * 3 * na,
+                                     cudaMemcpyHostToDevice, s));
+        const MeshView v = m.view();
+        P2M_TRY(launch_bvh_closest(v, pts.as<float>(), nullptr, nullptr, na, dd.as<float>(), nullptr, dt.as<int32_t>(),
+                                   nullptr, status, s));
+        std::vector<int32_t> tri(na);
+        P2M_CUDA_TRY(cudaMemcpyAsync(tri.data(), dt.p, sizeof(int32_t) * na, cudaMemcpyDeviceToHost, s));
+        P2M_CUDA_TRY(cudaStreamSynchronize(s));
+        for (int a = 0; a < na; ++a) {
+            const int i = n_vsites + a;
+            const int f = tri[a];
+            double q[3], A[3], B[3], C[3], p[3];
+            for (int k = 0; k < 3; ++k) {
+                q[k] = m.site_pos[3 * i + k];
+                A[k] = m.verts[3 * (int64_t)m.tris[3 * f] + k];
+                B[k] = m.verts[3 * (int64_t)m.tris[3 * f + 1] + k];
+                C[k] = m.verts[3 * (int64_t)m.tris[3 * f + 2] + k];
+            }
+            closest_on_tri_f64(q, A, B, C, p);
+            for (int k = 0; k < 3; ++k) m.site_ref[3 * i + k] = p[k];
+        }
+    }
+    double t4 = ms_now();
+    st.ms_proj = t4 - t3;
+    // reference points for the query's initial bound: FP32 position + its rounding radius
+    {
+        std::vector<float4> rf(S);
+        for (int i = 0; i < S; ++i) {
+            const double* r = &m.site_ref[3 * i];
+            const float x = (float)r[0], y = (float)r[1], z = (float)r[2];
+            const double e = std::sqrt((x - r[0]) * (x - r[0]) + (y - r[1]) * (y - r[1]) + (z - r[2]) * (z - r[2]));
+            rf[i] = make_float4(x, y, z, (float)(e * 1.0001 + 1e-30));
+        }
+        P2M_TRY(m.d_refs.alloc(sizeof(float4) * S));
+        P2M_CUDA_TRY(cudaMemcpyAsync(m.d_refs.p, rf.data(), sizeof(float4) * S, cudaMemcpyHostToDevice, s));
+        P2M_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    // corner balls (Eq. 3 for vertex sites, Eq. 8 for auxiliary sites); a ball contained in
+    // another ball of the same site adds nothing to the union and is dropped
+    m.ball_off.assign(S + 1, 0);
+    m.ball_c.clear();
+    m.ball_r.clear();
+    {
+        std::vector<double> uc, ur;
+        std::vector<char> keep;
+        for (int i = 0; i < S; ++i) {
+            const double* v = &m.site_ref[3 * i];
+            const int64_t c0 = ss.cell_off[i], c1 = ss.cell_off[i + 1];
+            uc.clear();
+            ur.clear();
+            if (m.site_kind[i] == 0) {
+                for (int64_t c = c0; c < c1; ++c) {
+                    const double* u = &ss.cell_xyz[3 * c];
+                    uc.insert(uc.end(), u, u + 3);
+                    ur.push_back(std::sqrt((u[0] - v[0]) * (u[0] - v[0]) + (u[1] - v[1]) * (u[1] - v[1]) + (u[2] - v[2]) * (u[2] - v[2])));
+                }
+                const int nb = (int)ur.size();
+                keep.assign(nb, 1);
+                for (int a = 0; a < nb; ++a) {
+                    for (int b = 0; b < nb && keep[a]; ++b) {
+                        if (a == b || !keep[b]) continue;
+                        const double dx = uc[3 * a] - uc[3 * b], dy = uc[3 * a + 1] - uc[3 * b + 1], dz = uc[3 * a + 2] - uc[3 * b + 2];
+                        const double d = std::sqrt(dx * dx + dy * dy + dz * dz);
+                        // a inside b (ties keep the lower index)
+                        if (d + ur[a] < ur[b] || (d + ur[a] == ur[b] && b < a)) keep[a] = 0;
+                    }
+                }
+                for (int a = 0; a < nb; ++a)
+                    if (keep[a]) {
+                        m.ball_c.insert(m.ball_c.end(), &uc[3 * a], &uc[3 * a] + 3);
+                        m.ball_r.push_back(ur[a]);
+                    }
+            } else {
+                double p[3];
+                for (int k = 0; k < 3; ++k) p[k] = m.site_pos[3 * i + k];
+                double r = 0;
+                for (int64_t c = c0; c < c1; ++c) {
+                    const double* u = &ss.cell_xyz[3 * c];
+                    const double a = std::sqrt((u[0] - p[0]) * (u[0] - p[0]) + (u[1] - p[1]) * (u[1] - p[1]) + (u[2] - p[2]) * (u[2] - p[2]));
+                    const double b = std::sqrt((u[0] - v[0]) * (u[0] - v[0]) + (u[1] - v[1]) * (u[1] - v[1]) + (u[2] - v[2]) * (u[2] - v[2]));
+                    r = std::max(r, a + b);
+                }
+                m.ball_c.insert(m.ball_c.end(), p, p + 3);
+                m.ball_r.push_back(r);
+            }
+            m.ball_off[i + 1] = (int64_t)m.ball_r.size();
+        }
+    }
+    const int64_t B = (int64_t)m.ball_r.size();
+    st.n_corners = B;
+    // FP32 balls for the device: centre rounded, radius inflated by the build slack, the
+    // centre's rounding and the FP32 error of the distance test
+    {
+        std::vector<float4> bf(B);
+        const double slack = (double)prm.build_eps_rel * m.diag;
+        for (int64_t b = 0; b < B; ++b) {
+            const double* u = &m.ball_c[3 * b];
+            const float x = (float)u[0], y = (float)u[1], z = (float)u[2];
+            const double e = std::sqrt((x - u[0]) * (x - u[0]) + (y - u[1]) * (y - u[1]) + (z - u[2]) * (z - u[2]));
+            const double mag = std::max(std::fabs(u[0]), std::max(std::fabs(u[1]), std::fabs(u[2])));
+            const double r = (m.ball_r[b] + e + slack + 4.8e-7 * (mag + m.ball_r[b] + m.diag)) * (1.0 + 1e-6);
+            bf[b] = make_float4(x, y, z, (float)r);
+        }
+        DevBuf d_balls, d_boff;
+        P2M_TRY(d_balls.alloc(sizeof(float4) * std::max<int64_t>(B, 1)));
+        P2M_TRY(d_boff.alloc(sizeof(int64_t) * (S + 1)));
+        P2M_CUDA_TRY(cudaMemcpyAsync(d_balls.p, bf.data(), sizeof(float4) * B, cudaMemcpyHostToDevice, s));
+        P2M_CUDA_TRY(cudaMemcpyAsync(d_boff.p, m.ball_off.data(), sizeof(int64_t) * (S + 1), cudaMemcpyHostToDevice, s));
+        const double t5 = ms_now();
+        P2M_TRY(build_lists(m, d_balls.as<float4>(), d_boff.as<int64_t>(), S, status, s));
+        P2M_TRY(check_status_word(h, s, "interception lists"));
+        st.ms_k1 = ms_now() - t5;
+    }
+    // nearest-site grid over D
+    {
+        const double t6 = ms_now();
+        double area = 0;
+        for (int64_t f = 0; f < m.n_tris; ++f) {
+            const float* a = &m.verts[3 * (int64_t)m.tris[3 * f]];
+            const float* b = &m.verts[3 * (int64_t)m.tris[3 * f + 1]];
+            const float* c = &m.verts[3 * (int64_t)m.tris[3 * f + 2]];
+            const double e0[3] = {(double)b[0] - a[0], (double)b[1] - a[1], (double)b[2] - a[2]};
+            const double e1[3] = {(double)c[0] - a[0], (double)c[1] - a[1], (double)c[2] - a[2]};
+            const double n[3] = {e0[1] * e1[2] - e0[2] * e1[1], e0[2] * e1[0] - e0[0] * e1[2], e0[0] * e1[1] - e0[1] * e1[0]};
+            area += 0.5 * std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        }
+        int G = prm.nn_grid_res;
+        if (G <= 0) {
+            const double spacing = std::sqrt(std::max(area, 1e-300) / std::max(1, n_vsites));
+            double ext = 0;
+            for (int k = 0; k < 3; ++k) ext = std::max(ext, m.dom_hi[k] - m.dom_lo[k]);
+            G = (int)std::lround(ext / (1.5 * spacing));
+            G = std::max(8, std::min(G, 192));
+        }
+        std::vector<float4> lo(S), hi(S);
+        for (int i = 0; i < S; ++i) {
+            lo[i] = make_float4(m.site_pos[3 * i], m.site_pos[3 * i + 1], m.site_pos[3 * i + 2], 0.f);
+            hi[i] = lo[i];
+        }
+        DevBuf dlo, dhi;
+        P2M_TRY(dlo.alloc(sizeof(float4) * S));
+        P2M_TRY(dhi.alloc(sizeof(float4) * S));
+        P2M_CUDA_TRY(cudaMemcpyAsync(dlo.p, lo.data(), sizeof(float4) * S, cudaMemcpyHostToDevice, s));
+        P2M_CUDA_TRY(cudaMemcpyAsync(dhi.p, hi.data(), sizeof(float4) * S, cudaMemcpyHostToDevice, s));
+        Bvh sb;
+        const float3 clo = make_float3((float)m.dom_lo[0], (float)m.dom_lo[1], (float)m.dom_lo[2]);
+        const float3 chi = make_float3((float)m.dom_hi[0], (float)m.dom_hi[1], (float)m.dom_hi[2]);
+        P2M_TRY(build_lbvh(dlo.as<float4>(), dhi.as<float4>(), S, clo, chi, sb, s));
+        P2M_TRY(build_grid(m, sb, G, status, s));
+        P2M_TRY(check_status_word(h, s, "nearest-site grid"));
+        st.ms_grid = ms_now() - t6;
+    }
     return P2M_OK;
 }
 
 }  // namespace p2m
+
+// ----------------------------------------------------------------------------- host-only API
+
+extern "C" int p2m_voronoi_cells(const float* h_sites, int64_t n, const double* dom_lo, const double* dom_hi, int seed,
+                                 float* h_sites_out, int64_t* h_corner_off, double* h_corners, int64_t* n_corners) {
+    using namespace p2m;
+    if (!h_sites || n < 4 || !dom_lo || !dom_hi || !n_corners) return fail(P2M_ERR_INVALID_ARG, "bad arguments");
+    SiteSet ss;
+    if (!ss.lat.setup(dom_lo, dom_hi)) return fail(P2M_ERR_INVALID_ARG, "bad domain");
+    uint64_t rng = mix64((uint64_t)seed * 0x100000001b3ull + 17);
+    for (int64_t i = 0; i < n; ++i) {
+        const double p[3] = {h_sites[3 * i], h_sites[3 * i + 1], h_sites[3 * i + 2]};
+        IPt q = ss.lat.to_lattice(p);
+        rng = mix64(rng);
+        q.x += (int64_t)(rng % 3) - 1;
+        q.y += (int64_t)((rng >> 8) % 3) - 1;
+        q.z += (int64_t)((rng >> 16) % 3) - 1;
+        if (!ss.lat.inside(q)) return fail(P2M_ERR_INVALID_ARG, "site outside the domain");
+        ss.pts.push_back(q);
+    }
+    std::string err;
+    ss.dt.init(ss.lat.R);
+    if (ss.triangulate_from(0, (uint64_t)seed, err)) return fail(P2M_ERR_INTERNAL, err);
+    if (ss.dt.validate(false)) return fail(P2M_ERR_INTERNAL, "triangulation failed its self-check");
+    ss.neighbour_csr();
+    double diag = 0;
+    for (int k = 0; k < 3; ++k) diag += (dom_hi[k] - dom_lo[k]) * (dom_hi[k] - dom_lo[k]);
+    if (ss.clip_cells(dom_lo, dom_hi, std::sqrt(diag), hardware_threads())) return fail(P2M_ERR_INTERNAL, "empty cell");
+    *n_corners = ss.cell_off[n];
+    if (h_sites_out)
+        for (int64_t i = 0; i < n; ++i) {
+            double w[3];
+            ss.world((int)i, w);
+            for (int k = 0; k < 3; ++k) h_sites_out[3 * i + k] = (float)w[k];
+        }
+    if (h_corner_off) std::memcpy(h_corner_off, ss.cell_off.data(), sizeof(int64_t) * (n + 1));
+    if (h_corners) std::memcpy(h_corners, ss.cell_xyz.data(), sizeof(double) * ss.cell_xyz.size());
+    return P2M_OK;
+}

@@ -1,20 +1,193 @@
-// Query path: nearest site (K2) + interception-list scan (K3), and the BVH search (K5) for
-// points outside the clipped domain.
+// Query path (Section 3.3 "Distance Query Stage"):
+//   K2  nearest site: one grid lookup, an FP32 scan of the cell's candidate sites, and an
+//       FP64 re-check when the two best are within 4e-6 (relative, squared) of each other;
+//       ties go to the lower site index.
+//   K3  list scan: the site's interception list, with bounding-sphere pruning ("Bounding
+//       Sphere Pruning"): a triangle is tested exactly only if ||q - c|| - r does not exceed
+//       the current bound.  The bound starts at the distance to the site's reference point on
+//       the mesh (an upper bound of d(q, M)), so pruning works from the first entry.  The
+//       minimum is taken over (squared distance, triangle id).
+//   K5  points outside the domain box D (or, defensively, whose list gave no triangle) are
+//       compacted and answered by the exact BVH search.
 #include "geom.cuh"
 #include "host.h"
 
 namespace p2m {
 
+enum { C_OUTSIDE = 0, C_SITES = 1, C_TIES = 2, C_ROWS = 3, C_EXACT = 4 };
+
+__device__ __forceinline__ bool grid_cell(const MeshView& m, float3 q, int& cell) {
+    const float fx = (q.x - m.lo.x) * m.inv_h.x;
+    const float fy = (q.y - m.lo.y) * m.inv_h.y;
+    const float fz = (q.z - m.lo.z) * m.inv_h.z;
+    // NaN fails every comparison and lands outside
+    if (!(fx >= 0.0f && fy >= 0.0f && fz >= 0.0f && fx < (float)m.G && fy < (float)m.G && fz < (float)m.G)) return false;
+    const int ix = min((int)fx, m.G - 1), iy = min((int)fy, m.G - 1), iz = min((int)fz, m.G - 1);
+    cell = (iz * m.G + iy) * m.G + ix;
+    return true;
+}
+
+// Nearest site among the grid cell's candidates.
+template <bool COUNT>
+__device__ __forceinline__ int nearest_site(const MeshView& m, float3 q, int cell, unsigned long long* counters) {
+    const int j0 = __ldg(m.cell_off + cell), j1 = __ldg(m.cell_off + cell + 1);
+    float bd = INFINITY, sd = INFINITY;
+    int bs = -1;
+    for (int j = j0; j < j1; ++j) {
+        const int s = __ldg(m.cell_site + j);
+        const float4 p = __ldg(m.sites + s);
+        const float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
+        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        if (d2 < bd || (d2 == bd && s < bs)) {
+            sd = bd;
+            bd = d2;
+            bs = s;
+        } else if (d2 < sd) {
+            sd = d2;
+        }
+    }
+    if (COUNT) atomicAdd(counters + C_SITES, (unsigned long long)(j1 - j0));
+    if (sd <= bd * (1.0f + 4e-6f) + 1e-30f) {
+        // near tie: decide in FP64 (differences of FP32 coordinates are exact in FP64)
+        if (COUNT) atomicAdd(counters + C_TIES, 1ull);
+        const float lim = bd * (1.0f + 8e-6f) + 1e-30f;
+        double best = 1e300;
+        int bi = -1;
+        for (int j = j0; j < j1; ++j) {
+            const int s = __ldg(m.cell_site + j);
+            const float4 p = __ldg(m.sites + s);
+            const float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
+            if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) > lim) continue;
+            const double ex = (double)q.x - (double)p.x, ey = (double)q.y - (double)p.y, ez = (double)q.z - (double)p.z;
+            const double d2 = ex * ex + ey * ey + ez * ez;
+            if (d2 < best || (d2 == best && s < bi)) { best = d2; bi = s; }
+        }
+        bs = bi;
+    }
+    return bs;
+}
+
+// Scan of one interception list; returns the (d2, tri) key and the (s, t) of the winner.
+template <bool COUNT>
+__device__ __forceinline__ unsigned long long scan_list(const MeshView& m, float3 q, int site, float& bs, float& bt,
+                                                        unsigned long long* counters) {
+    const int r0 = __ldg(m.row_off + site), r1 = __ldg(m.row_off + site + 1);
+    const float4 ref = __ldg(m.refs + site);
+    const float rx = q.x - ref.x, ry = q.y - ref.y, rz = q.z - ref.z;
+    float bound = sqrtf(fmaf(rx, rx, fmaf(ry, ry, rz * rz))) + ref.w;
+    bound = fmaf(bound, 1.0f + 9.6e-7f, m.prune_abs);
+    unsigned long long best = ~0ull;
+    int n_exact = 0;
+    for (int j = r0; j < r1; ++j) {
+        const int f = __ldg(m.row_tri + j);
+        const float4 sp = __ldg(m.tsph + f);
+        const float dx = q.x - sp.x, dy = q.y - sp.y, dz = q.z - sp.z;
+        const float lim = bound + sp.w;
+        if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) > lim * lim) continue;
+        if (COUNT) ++n_exact;
+        const TriRec T = load_tri(m.tri, f);
+        float s, t;
+        const float d2 = tri_dist2(q, T, s, t);
+        const unsigned long long key = dist_key(d2, f);
+        if (key < best) {
+            best = key;
+            bs = s;
+            bt = t;
+            bound = fminf(bound, fmaf(sqrtf(d2), 1.0f + 9.6e-7f, m.prune_abs));
+        }
+    }
+    if (COUNT) {
+        atomicAdd(counters + C_ROWS, (unsigned long long)(r1 - r0));
+        atomicAdd(counters + C_EXACT, (unsigned long long)n_exact);
+    }
+    return best;
+}
+
+__device__ __forceinline__ void write_result(const MeshView& m, int64_t i, unsigned long long key, float s, float t,
+                                             float* __restrict__ dist, float* __restrict__ closest,
+                                             int32_t* __restrict__ tri_out, float* __restrict__ bary) {
+    const int f = (int)(key & 0xffffffffu);
+    dist[i] = sqrtf(__uint_as_float((unsigned)(key >> 32)));
+    if (tri_out) tri_out[i] = f;
+    if (closest) {
+        const TriRec T = load_tri(m.tri, f);
+        const float3 p = tri_point(T, s, t);
+        closest[3 * i] = p.x;
+        closest[3 * i + 1] = p.y;
+        closest[3 * i + 2] = p.z;
+    }
+    if (bary) {
+        bary[3 * i] = 1.0f - s - t;
+        bary[3 * i + 1] = s;
+        bary[3 * i + 2] = t;
+    }
+}
+
+// Thread-per-query schedule: fused nearest-site search and list scan.
+template <bool COUNT>
+__global__ void __launch_bounds__(256) k_query_thread(MeshView m, const float* __restrict__ pts, int64_t n,
+                                                     float* __restrict__ dist, float* __restrict__ closest,
+                                                     int32_t* __restrict__ tri_out, float* __restrict__ bary,
+                                                     int32_t* __restrict__ rest, int* __restrict__ n_rest,
+                                                     unsigned long long* counters) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float3 q = make_float3(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]);
+        int cell;
+        int site = -1;
+        if (grid_cell(m, q, cell)) site = nearest_site<COUNT>(m, q, cell, counters);
+        unsigned long long key = ~0ull;
+        float s = 0.0f, t = 0.0f;
+        if (site >= 0) key = scan_list<COUNT>(m, q, site, s, t, counters);
+        if (key == ~0ull) {
+            rest[atomicAdd(n_rest, 1)] = (int32_t)i;
+            if (COUNT) atomicAdd(counters + C_OUTSIDE, 1ull);
+            continue;
+        }
+        write_result(m, i, key, s, t, dist, closest, tri_out, bary);
+    }
+}
+
+__global__ void k_site_only(MeshView m, const float* __restrict__ pts, int64_t n, int32_t* __restrict__ site_out) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float3 q = make_float3(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]);
+        int cell;
+        site_out[i] = grid_cell(m, q, cell) ? nearest_site<false>(m, q, cell, nullptr) : -1;
+    }
+}
+
+int query_grid_blocks(int64_t n, int threads) {
+    const int64_t want = (n + threads - 1) / threads;
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, 152LL * 64));
+}
+
 int run_query(p2m_index* h, MeshData& m, const float* d_pts, int64_t n, float* d_dist, float* d_closest,
               int32_t* d_tri, float* d_bary, unsigned long long* counters, cudaStream_t s) {
-    (void)counters;
     const MeshView v = m.view();
-    return launch_bvh_closest(v, d_pts, nullptr, n, d_dist, d_closest, d_tri, d_bary, index_status(h), s);
+    if (v.G == 0) return launch_bvh_closest(v, d_pts, nullptr, nullptr, n, d_dist, d_closest, d_tri, d_bary, index_status(h), s);
+    DevBuf& rest = index_rest(h);
+    P2M_TRY(rest.ensure(sizeof(int32_t) * (n + 64)));
+    int* n_rest = reinterpret_cast<int*>(rest.as<char>() + sizeof(int32_t) * (n + 32));
+    P2M_CUDA_TRY(cudaMemsetAsync(n_rest, 0, sizeof(int), s));
+    const int threads = 256;
+    const int blocks = query_grid_blocks(n, threads);
+    if (counters)
+        k_query_thread<true><<<blocks, threads, 0, s>>>(v, d_pts, n, d_dist, d_closest, d_tri, d_bary, rest.as<int32_t>(),
+                                                        n_rest, counters);
+    else
+        k_query_thread<false><<<blocks, threads, 0, s>>>(v, d_pts, n, d_dist, d_closest, d_tri, d_bary, rest.as<int32_t>(),
+                                                         n_rest, nullptr);
+    P2M_CUDA_TRY(cudaGetLastError());
+    // the points left over take the exact BVH search; the count stays on the device
+    return launch_bvh_closest(v, d_pts, rest.as<int32_t>(), n_rest, n, d_dist, d_closest, d_tri, d_bary, index_status(h), s);
 }
 
 int run_nearest_site(p2m_index* h, MeshData& m, const float* d_pts, int64_t n, int32_t* d_site, cudaStream_t s) {
-    (void)h; (void)m; (void)d_pts; (void)n; (void)d_site; (void)s;
-    return fail(P2M_ERR_NOT_IMPLEMENTED, "nearest-site search not built yet");
+    (void)h;
+    const MeshView v = m.view();
+    if (v.G == 0) return fail(P2M_ERR_INVALID_ARG, "index has no nearest-site grid");
+    k_site_only<<<query_grid_blocks(n, 256), 256, 0, s>>>(v, d_pts, n, d_site);
+    P2M_CUDA_TRY(cudaGetLastError());
+    return P2M_OK;
 }
 
 }  // namespace p2m

@@ -1,0 +1,142 @@
+// Host stage of the build: sites on a lattice, their exact Delaunay triangulation, the
+// clipped Voronoi cells (FP64) and the corner balls of Eq. 3 / Eq. 8.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <cstring>
+#include <thread>
+
+#include "host_geom.h"
+#include "voronoi.h"
+
+namespace p2m {
+
+static inline uint64_t mix64(uint64_t z) {
+    z += 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+}
+
+static inline uint64_t morton_key(const IPt& p, int64_t R) {
+    auto spread = [](uint64_t v) {
+        v &= 0x1fffff;
+        v = (v | v << 32) & 0x1f00000000ffffull;
+        v = (v | v << 16) & 0x1f0000ff0000ffull;
+        v = (v | v << 8) & 0x100f00f00f00f00full;
+        v = (v | v << 4) & 0x10c30c30c30c30c3ull;
+        v = (v | v << 2) & 0x1249249249249249ull;
+        return v;
+    };
+    return (spread((uint64_t)(p.x + R)) << 2) | (spread((uint64_t)(p.y + R)) << 1) | spread((uint64_t)(p.z + R));
+}
+
+void SiteSet::world(int i, double out[3]) const { lat.to_world(pts[i], out); }
+
+// Insert sites [first, pts.size()) into the triangulation in Morton order; a site whose
+// insertion fails (flat tetrahedron or exact duplicate) is moved by one lattice step.
+int SiteSet::triangulate_from(int first, uint64_t seed, std::string& err) {
+    std::vector<std::pair<uint64_t, int>> order;
+    for (int i = first; i < (int)pts.size(); ++i) order.push_back({morton_key(pts[i], lat.R), i});
+    std::sort(order.begin(), order.end());
+    uint64_t rng = mix64(seed ^ 0x5eedull);
+    vid.resize(pts.size(), -1);
+    for (auto& o : order) {
+        const int i = o.second;
+        int tries = 0;
+        while (true) {
+            const int r = dt.insert(pts[i], rng);
+            if (r >= 0) { vid[i] = r; break; }
+            if (r == INSERT_BROKEN) { err = "Delaunay insertion broke the triangulation"; return -1; }
+            if (++tries > 64) { err = "could not place a site after 64 jitters"; return -1; }
+            rng = mix64(rng);
+            IPt p = pts[i];
+            p.x += (int64_t)(rng % 3) - 1;
+            p.y += (int64_t)((rng >> 8) % 3) - 1;
+            p.z += (int64_t)((rng >> 16) % 3) - 1;
+            if (lat.inside(p)) pts[i] = p;
+        }
+    }
+    return 0;
+}
+
+void SiteSet::neighbour_csr() {
+    // Delaunay vertex ids are 4 + insertion position; map them back to site ids
+    std::vector<int> site_of(dt.pts.size(), -1);
+    for (int i = 0; i < (int)vid.size(); ++i) site_of[vid[i]] = i;
+    std::vector<int64_t> off;
+    std::vector<int32_t> nb;
+    dt.neighbours((int)dt.pts.size() - dt.n_super, off, nb);
+    const int n = (int)pts.size();
+    nb_off.assign(n + 1, 0);
+    nb_id.clear();
+    std::vector<std::vector<int32_t>> tmp(n);
+    for (int v = 0; v + dt.n_super < (int)dt.pts.size(); ++v) {
+        const int s = site_of[v + dt.n_super];
+        if (s < 0) continue;
+        for (int64_t k = off[v]; k < off[v + 1]; ++k) {
+            const int t = site_of[nb[k] + dt.n_super];
+            if (t >= 0) tmp[s].push_back(t);
+        }
+    }
+    for (int s = 0; s < n; ++s) {
+        nb_off[s + 1] = nb_off[s] + (int64_t)tmp[s].size();
+        nb_id.insert(nb_id.end(), tmp[s].begin(), tmp[s].end());
+    }
+}
+
+// Corners of every site's cell: D cut by the bisectors of its Delaunay neighbours,
+// nearest neighbour first.  Threads split the sites.
+int SiteSet::clip_cells(const double dom_lo[3], const double dom_hi[3], double diag, int n_threads) {
+    const int n = (int)pts.size();
+    cell_off.assign(n + 1, 0);
+    std::vector<std::vector<double>> corners(n);
+    std::atomic<int> next(0), bad(0);
+    const double tol = 1e-12 * diag;
+    auto work = [&]() {
+        Clipper C;
+        std::vector<std::pair<double, int>> order;
+        while (true) {
+            const int s = next.fetch_add(1);
+            if (s >= n) break;
+            double ps[3];
+            world(s, ps);
+            C.box(dom_lo, dom_hi);
+            order.clear();
+            for (int64_t k = nb_off[s]; k < nb_off[s + 1]; ++k) {
+                double pt[3];
+                world(nb_id[k], pt);
+                const double d2 = (pt[0] - ps[0]) * (pt[0] - ps[0]) + (pt[1] - ps[1]) * (pt[1] - ps[1]) +
+                                  (pt[2] - ps[2]) * (pt[2] - ps[2]);
+                order.push_back({d2, nb_id[k]});
+            }
+            std::sort(order.begin(), order.end());
+            for (auto& o : order) {
+                double pt[3];
+                world(o.second, pt);
+                double nrm[3] = {pt[0] - ps[0], pt[1] - ps[1], pt[2] - ps[2]};
+                const double len = std::sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
+                if (!(len > 0)) continue;
+                for (double& c : nrm) c /= len;
+                const double d = 0.5 * (nrm[0] * (pt[0] + ps[0]) + nrm[1] * (pt[1] + ps[1]) + nrm[2] * (pt[2] + ps[2]));
+                if (!C.clip(nrm, d, tol)) { bad.fetch_add(1); break; }
+            }
+            corners[s] = C.V;
+        }
+    };
+    std::vector<std::thread> th;
+    for (int t = 0; t < std::max(1, n_threads); ++t) th.emplace_back(work);
+    for (auto& t : th) t.join();
+    if (bad.load()) return -1;
+    for (int s = 0; s < n; ++s) cell_off[s + 1] = cell_off[s] + (int64_t)(corners[s].size() / 3);
+    cell_xyz.resize(cell_off[n] * 3);
+    for (int s = 0; s < n; ++s) std::copy(corners[s].begin(), corners[s].end(), cell_xyz.begin() + cell_off[s] * 3);
+    return 0;
+}
+
+int hardware_threads() {
+    const unsigned h = std::thread::hardware_concurrency();
+    return (int)std::max(1u, std::min(h, 64u));
+}
+
+}  // namespace p2m

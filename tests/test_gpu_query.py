@@ -1,0 +1,167 @@
+"""GPU parity of the full query path (nearest site -> interception-list scan) against the FP64
+oracle, plus the structural checks that make the localised search exact:
+
+* K2 nearest site equals the brute-force nearest site over the index's own sites;
+* K1 list sandwich: for every site, {f : d(u,f) <= r_u - e} <= row <= {f : d(u,f) <= r_u + slack + e}
+  over its balls (brute force over all triangles);
+* completeness: the oracle's closest triangle is in the list of the oracle's nearest site;
+* results: |d - d_oracle| <= 1e-6 diag, triangle id equal unless the oracle's two best are
+  within that tolerance, closest point within 2e-6 diag, barycentrics consistent.
+"""
+import numpy as np
+import pytest
+
+import oracle
+import p2m_workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def p2m():
+    from paper_2605_00429_gb300 import build as b
+    b.build()
+    import paper_2605_00429_gb300 as p
+    return p
+
+
+def _query(idx, q):
+    import torch
+    d, c, t, b = idx.query(torch.from_numpy(np.ascontiguousarray(q)).cuda())
+    torch.cuda.synchronize()
+    return d.cpu().numpy(), c.cpu().numpy(), t.cpu().numpy(), b.cpu().numpy()
+
+
+def check_parity(mesh, q, out, ref=None):
+    d, c, t, b = out
+    if ref is None:
+        ref = oracle.closest(mesh.verts, mesh.tris, q)
+    diag = mesh.diag()
+    tol = 1e-6 * diag
+    err = np.abs(d.astype(np.float64) - ref["dist"])
+    assert np.max(err) <= tol, f"distance error {np.max(err):.3e} > {tol:.3e} at {np.argmax(err)}"
+    tie = (ref["dist2"] - ref["dist"]) <= tol
+    wrong = (t != ref["tri"]) & ~tie
+    assert not wrong.any(), f"{wrong.sum()} triangle ids differ"
+    assert np.max(np.linalg.norm(c - ref["closest"], axis=1)[~tie], initial=0) <= 2 * tol
+    v = mesh.verts.astype(np.float64)
+    p = np.einsum("nk,nkc->nc", b.astype(np.float64), v[mesh.tris[t]])
+    assert np.max(np.linalg.norm(p - c, axis=1)) <= 2 * tol
+    assert np.all(b >= -1e-5) and np.max(np.abs(b.sum(1) - 1)) < 1e-5
+    return ref
+
+
+def check_structure(p2m, idx, mesh, q, n_sites_check=None, rng=None):
+    import torch
+    sites, ref_pts, kind = idx.sites()
+    s_gpu = idx.nearest_site(torch.from_numpy(np.ascontiguousarray(q)).cuda()).cpu().numpy()
+    s_orc, d1, d2 = oracle.nearest_site(sites.astype(np.float64), q.astype(np.float64))
+    assert np.array_equal(s_gpu, s_orc), f"{(s_gpu != s_orc).sum()} nearest sites differ"
+    off, ids = idx.lists()
+    ref = oracle.closest(mesh.verts, mesh.tris, q)
+    # completeness: the true closest triangle (or a tied one) is in the nearest site's list
+    tol = 1e-6 * mesh.diag()
+    for j in range(len(q)):
+        row = ids[off[s_orc[j]]:off[s_orc[j] + 1]]
+        if ref["tri"][j] in row:
+            continue
+        # a tie: some triangle in the row must reach the same distance
+        r = oracle.closest(mesh.verts, mesh.tris[row], q[j:j + 1])
+        assert r["dist"][0] <= ref["dist"][j] + tol, f"query {j}: closest triangle missing from its site's list"
+    # list sandwich on a sample of sites
+    boff, bc, br = idx.balls()
+    S = len(sites)
+    rng = rng or np.random.default_rng(0)
+    pick = np.arange(S) if n_sites_check is None or n_sites_check >= S else rng.choice(S, n_sites_check, replace=False)
+    eps = 1e-6 * mesh.diag()
+    for s in pick:
+        mg = oracle.ball_margin(mesh.verts, mesh.tris, bc[boff[s]:boff[s + 1]], br[boff[s]:boff[s + 1]])
+        row = set(ids[off[s]:off[s + 1]].tolist())
+        must = set(np.nonzero(mg <= -eps)[0].tolist())
+        may = set(np.nonzero(mg <= 2e-6 * mesh.diag() + eps)[0].tolist())
+        assert must <= row, f"site {s}: {len(must - row)} triangles missing"
+        assert row <= may, f"site {s}: {len(row - may)} extra triangles"
+    # Eq. 8 radius of auxiliary sites
+    for s in np.nonzero(kind == 1)[0][:50]:
+        assert boff[s + 1] - boff[s] == 1
+    return ref
+
+
+def test_small_uv_sphere_full(p2m):
+    """UV sphere (960 tris), 100k queries uniform in the 1.2x bbox: every query vs the oracle."""
+    mesh, q = W.workload_small(100_000)
+    idx = p2m.P2MIndex(mesh.verts, mesh.tris)
+    check_parity(mesh, q, _query(idx, q))
+    st = idx.stats()
+    assert st["n_sites"] >= 482 and st["nnz"] > 0
+
+
+def test_small_uv_sphere_structure(p2m):
+    mesh, q = W.workload_small(4000, seed=1)
+    idx = p2m.P2MIndex(mesh.verts, mesh.tris)
+    check_structure(p2m, idx, mesh, q, n_sites_check=120)
+
+
+@pytest.mark.parametrize("aux", [0, 1])
+def test_noisy_icosphere_small(p2m, aux):
+    mesh, q = W.workload_large(20_000, k=3)
+    idx = p2m.P2MIndex(mesh.verts, mesh.tris, enable_aux=aux)
+    check_parity(mesh, q, _query(idx, q))
+    check_structure(p2m, idx, mesh, q[:2000], n_sites_check=80)
+
+
+def test_cylinder_cone_small(p2m):
+    mesh, q = W.workload_symmetric(20_000, n_ang=48, n_ax=12)
+    idx = p2m.P2MIndex(mesh.verts, mesh.tris)
+    check_parity(mesh, q, _query(idx, q))
+    check_structure(p2m, idx, mesh, q[:2000], n_sites_check=80)
+
+
+def test_cube_and_plane_closed_forms(p2m):
+    """Meshes with closed-form distances, through the full GPU path."""
+    cube = W.unit_cube()
+    rng = np.random.default_rng(3)
+    q = (rng.random((20000, 3)) * 1.6 - 0.8).astype(np.float32)
+    d, c, t, b = _query(p2m.P2MIndex(cube.verts, cube.tris), q)
+    a = np.abs(q.astype(np.float64))
+    inside = np.all(a <= 0.5, 1)
+    expect = np.where(inside, 0.5 - a.max(1), np.linalg.norm(np.maximum(a - 0.5, 0), axis=1))
+    assert np.max(np.abs(d - expect)) <= 1e-6 * cube.diag()
+    plane = W.square_plane(1.0)
+    q = (rng.random((20000, 3)) * np.array([2.4, 2.4, 1.0]) - np.array([1.2, 1.2, 0.5])).astype(np.float32)
+    d, c, t, b = _query(p2m.P2MIndex(plane.verts, plane.tris), q)
+    qd = q.astype(np.float64)
+    expect = np.sqrt(np.maximum(np.abs(qd[:, 0]) - 1, 0) ** 2 + np.maximum(np.abs(qd[:, 1]) - 1, 0) ** 2 + qd[:, 2] ** 2)
+    assert np.max(np.abs(d - expect)) <= 1e-6 * plane.diag()
+
+
+def test_edge_cases(p2m):
+    import torch
+    mesh, _ = W.workload_small(10)
+    idx = p2m.P2MIndex(mesh.verts, mesh.tris)
+    # empty query
+    d, c, t, b = idx.query(torch.empty(0, 3, device="cuda"))
+    assert d.numel() == 0
+    # far outside the domain box: exact BVH path
+    q = np.array([[100.0, -50.0, 3.0], [0.0, 0.0, 7.0], [-3.0, -3.0, -3.0], [0.0, 0.0, 0.0]], np.float32)
+    check_parity(mesh, q, _query(idx, q))
+    # ragged sizes around block boundaries
+    for n in (1, 31, 255, 257, 1023):
+        qq = W.queries_uniform_box(mesh, n, 1.3, seed=n)
+        check_parity(mesh, qq, _query(idx, qq))
+    # bad input is reported, not crashed on
+    with pytest.raises(p2m.P2MError):
+        p2m.P2MIndex(mesh.verts, np.array([[0, 1, 99999]], np.int32))
+    bad = mesh.verts.copy()
+    bad[3, 1] = np.nan
+    with pytest.raises(p2m.P2MError):
+        p2m.P2MIndex(bad, mesh.tris)
+
+
+def test_counters(p2m):
+    import torch
+    mesh, q = W.workload_small(20000)
+    idx = p2m.P2MIndex(mesh.verts, mesh.tris)
+    c = idx.counters(torch.from_numpy(q).cuda())
+    assert c["n_queries"] == 20000 and c["row_entries"] >= c["exact_tests"] > 0
+    assert c["site_candidates"] >= 20000 - c["n_outside"]
