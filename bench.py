@@ -1,0 +1,332 @@
+#!/usr/bin/env python
+"""Benchmark of the P2M++ query path on GB300.
+
+One step = one closest-point query pass (nearest site + interception-list scan, every
+query answered) over the workload's full query set, inputs resident in HBM.  Default
+workload: icosphere(6) with 3-octave value noise (81,920 triangles), 10M queries (half
+uniform in the 1.2x bbox, half surface + N(0, (0.01 diag)^2)).  The index is built once
+before timing; its CSR build time is reported separately, as are fwd+bwd throughput on the
+differentiation workload (icosphere(5), 1M near-surface queries, L = sum d^2) and the
+end-to-end rate through the host-buffer C-ABI call.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+
+Prints one JSON line (rank 0).  With --impl reference the FP64 brute-force oracle is timed
+on the host cores on bounded samples of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import p2m_workloads as W  # noqa: E402
+
+PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
+SM_COUNT = 152
+FP32_LANES_PER_SM = 128
+# algorithmic FP32 work model (FLOP, an FMA counts 2): see DESIGN.md "Roofline"
+FLOP_PER_SITE = 8
+FLOP_PER_ROW_ENTRY = 10
+FLOP_PER_EXACT = 80
+FLOP_PER_QUERY = 26
+BYTES_PER_QUERY = 12 + 32  # FP32 point in; dist, closest[3], tri, bary[3] out
+
+WORKLOADS = {
+    "large": ("icosphere(6) + 3-octave noise a=0.05, 81,920 tris; 10M queries: 50% uniform in 1.2x bbox, "
+              "50% surface + N(0,(0.01 diag)^2); seed 0", lambda n: W.workload_large(n or 10_000_000)),
+    "small": ("UV sphere 32x16, 960 tris; 100k queries uniform in 1.2x bbox; seed 0",
+              lambda n: W.workload_small(n or 100_000)),
+    "symmetric": ("cylinder+cone 512x128, 203,776 tris, aux on; 10M queries: 70% within 0.02 diag of the surface, "
+                  "30% uniform in 1.2x bbox; seed 0", lambda n: W.workload_symmetric(n or 10_000_000)),
+    "diff": ("icosphere(5) + noise, 20,480 tris; 1M queries surface + N(0,(0.01 diag)^2); seed 0",
+             lambda n: W.workload_diff(n or 1_000_000)),
+}
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def peaks():
+    try:
+        with open(PEAKS_FILE) as fh:
+            p = json.load(fh)
+        return p, "measured"
+    except (OSError, ValueError):
+        return {"hbm_gbs": 6800.0, "sm_max_mhz": 2070.0}, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi clock / throttle-reason samples during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index: int):
+        self.gpu = gpu_index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except OSError:
+            self.p = None
+        time.sleep(0.15)
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
+        time.sleep(0.15)
+        self.p.terminate()
+        out, _ = self.p.communicate(timeout=10)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            parts = [x.strip() for x in line.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def cpu_baseline(mesh, q, target_s=12.0, seed=0):
+    """The FP64 oracle (as it stands) on a bounded random sample of the workload's queries."""
+    import oracle
+    rng = np.random.default_rng(seed + 99)
+    probe = q[rng.choice(len(q), min(len(q), 256), replace=False)]
+    t = time.perf_counter()
+    oracle.closest(mesh.verts, mesh.tris, probe)
+    per_q = max((time.perf_counter() - t) / len(probe), 1e-9)
+    n = int(min(len(q), max(256, target_s / per_q)))
+    sample = q[rng.choice(len(q), n, replace=False)]
+    t = time.perf_counter()
+    oracle.closest(mesh.verts, mesh.tris, sample)
+    dt = time.perf_counter() - t
+    return {"value": n / dt, "unit": "queries/s", "cores": oracle.num_threads(), "kind": "oracle",
+            "sample": f"{n} random queries of the workload, FP64 brute force over all {mesh.n_tris} triangles",
+            "seconds": dt}
+
+
+def run_reference(args, rank, world):
+    """Reference arm: the FP64 oracle timed on the host cores, same metric."""
+    if rank != 0:
+        return
+    desc, make = WORKLOADS[args.config]
+    mesh, q = make(args.queries)
+    import oracle
+    oracle.build()
+    steps, warm = args.steps, args.warmup
+    rng = np.random.default_rng(5)
+    probe = q[rng.choice(len(q), 256, replace=False)]
+    t = time.perf_counter()
+    oracle.closest(mesh.verts, mesh.tris, probe)
+    per_q = (time.perf_counter() - t) / 256
+    budget = 150.0 / max(1, steps + warm)  # the whole run stays within a few minutes
+    n = int(max(64, min(len(q), budget / max(per_q, 1e-9))))
+    times = []
+    for k in range(warm + steps):
+        sample = q[rng.choice(len(q), n, replace=False)]
+        t = time.perf_counter()
+        oracle.closest(mesh.verts, mesh.tris, sample)
+        if k >= warm:
+            times.append(time.perf_counter() - t)
+    ms = float(np.mean(times)) * 1e3
+    value = n / (ms / 1e3)
+    line = {"impl": "reference", "metric": "closest-point queries/s", "value": value, "unit": "queries/s",
+            "n_gpus": world, "steps": steps, "warmup": warm, "ms_per_step": ms, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": desc, "queries_per_step": n},
+            "cpu_baseline": {"value": value, "unit": "queries/s", "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"{n} random queries per step, FP64 brute force over all {mesh.n_tris} triangles"},
+            "e2e": {"value": value, "unit": "queries/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=50)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--config", default="large", choices=sorted(WORKLOADS))
+    ap.add_argument("--queries", type=int, default=0, help="override the workload's query count")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true", help="skip fwd+bwd and e2e legs")
+    ap.add_argument("--schedule", type=int, default=0)
+    args = ap.parse_args()
+    args.warmup = max(args.warmup, 3)
+
+    rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    else:
+        torch.cuda.set_device(0)
+    dev = torch.device("cuda", torch.cuda.current_device())
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+
+    from paper_2605_00429_gb300 import build as pbuild
+    if rank == 0 or world == 1:
+        pbuild.build()
+    barrier()
+    import paper_2605_00429_gb300 as p2m
+
+    desc, make = WORKLOADS[args.config]
+    mesh, q = make(args.queries)
+    n = q.shape[0]
+    t0 = time.perf_counter()
+    idx = p2m.P2MIndex(mesh.verts, mesh.tris, schedule=args.schedule)
+    build_wall_ms = (time.perf_counter() - t0) * 1e3
+    st = idx.stats()
+    pts = torch.from_numpy(q).to(dev)
+    out = (torch.empty(n, device=dev), torch.empty(n, 3, device=dev), torch.empty(n, device=dev, dtype=torch.int32),
+           torch.empty(n, 3, device=dev))
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device=dev)  # 256 MB > 129 MB L2
+
+    for _ in range(args.warmup):
+        idx.query(pts, out=out)
+    torch.cuda.synchronize()
+
+    # instrumented pass (untimed): work counters for the algorithmic FLOP count
+    cnt = idx.counters(pts)
+    torch.cuda.synchronize()
+
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    sampler = ClockSampler(torch.cuda.current_device())
+    sampler.start()
+    barrier()
+    torch.cuda.synchronize()
+    for k in range(args.steps):
+        flush.zero_()  # L2 flush between timed steps (outside the events)
+        starts[k].record(stream)
+        idx.query(pts, out=out)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    barrier()
+    clocks = sampler.stop()
+    step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    ms = float(np.mean(step_ms))
+    if world > 1:
+        t = torch.tensor([ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    value = world * n / (ms / 1e3)
+
+    pk, pk_kind = peaks()
+    sm_max = float(pk.get("sm_max_mhz", 2070.0))
+    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    flops = (FLOP_PER_SITE * cnt["site_candidates"] + FLOP_PER_ROW_ENTRY * cnt["row_entries"] +
+             FLOP_PER_EXACT * cnt["exact_tests"] + FLOP_PER_QUERY * n)
+    achieved = flops / (ms / 1e3) / 1e12
+    hbm_gbs = BYTES_PER_QUERY * n / (ms / 1e3) / 1e9
+
+    line = {"metric": "closest-point queries/s (10M pts, 82k tris)" if args.config == "large" else
+            "closest-point queries/s", "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": desc, "queries": n, "tris": mesh.n_tris, "l2": "flushed between steps (256 MB write)",
+                       "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
+            "gpu_launches": 2 * args.steps,
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
+                         "frac": achieved / alu_peak, "traffic": None, "kernel": "k_query_thread",
+                         "peak_kind": f"FP32 FMA lanes x max SM clock from {pk_kind} peaks",
+                         "hbm_achieved_gbs": hbm_gbs, "hbm_peak_gbs": pk.get("hbm_gbs"),
+                         "hbm_frac": hbm_gbs / float(pk.get("hbm_gbs", 6800.0))},
+            "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
+            "csr_build_ms": st["ms_tri"] + st["ms_lbvh"] + st["ms_k1"],
+            "build": {"wall_ms": build_wall_ms, "host_delaunay_ms": st["ms_delaunay"], "host_aug_ms": st["ms_aug"],
+                      "host_cells_ms": st["ms_cells"], "gpu_lists_ms": st["ms_k1"], "gpu_grid_ms": st["ms_grid"],
+                      "sites": st["n_sites"], "aux_sites": st["n_aux_sites"], "nnz": st["nnz"],
+                      "max_list": st["max_row"], "avg_list": st["avg_row"], "grid": st["grid_res"]},
+            "counters": {"queried_entries": cnt["row_entries"] / n, "queried_exact": cnt["exact_tests"] / n,
+                         "sites_per_query": cnt["site_candidates"] / n, "outside": cnt["n_outside"],
+                         "tie_rechecks": cnt["tie_rechecks"]}}
+
+    if not args.no_extras:
+        # end to end through the host-buffer C-ABI call: pinned inputs, all four outputs back
+        hp = torch.from_numpy(q).pin_memory()
+        hd = torch.empty(n, dtype=torch.float32).pin_memory()
+        hc = torch.empty(n, 3, dtype=torch.float32).pin_memory()
+        ht = torch.empty(n, dtype=torch.int32).pin_memory()
+        hb = torch.empty(n, 3, dtype=torch.float32).pin_memory()
+        idx.query_host(hp, hd, hc, ht, hb)
+        e2e_steps = max(1, min(args.steps, 10))
+        barrier()
+        t = time.perf_counter()
+        for _ in range(e2e_steps):
+            idx.query_host(hp, hd, hc, ht, hb)
+        e2e_s = (time.perf_counter() - t) / e2e_steps
+        line["e2e"] = {"value": world * n / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": 12 * n,
+                       "d2h_bytes_per_step": 32 * n}
+        # fwd + bwd on the differentiation workload
+        dm, dq = W.workload_diff(1_000_000)
+        didx = p2m.P2MIndex(dm.verts, dm.tris)
+        verts = torch.from_numpy(dm.verts).to(dev).requires_grad_(True)
+        dpts = torch.from_numpy(dq).to(dev).requires_grad_(True)
+
+        def fb():
+            d = p2m.unsigned_distance(dpts, verts, didx)
+            loss = (d * d).sum()
+            loss.backward()
+            return loss
+        for _ in range(3):
+            fb()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        fsteps = max(3, min(args.steps, 20))
+        e0.record()
+        for _ in range(fsteps):
+            verts.grad = None
+            dpts.grad = None
+            fb()
+        e1.record()
+        torch.cuda.synchronize()
+        fb_ms = e0.elapsed_time(e1) / fsteps
+        line["fwd_bwd"] = {"value": dq.shape[0] / (fb_ms / 1e3), "unit": "queries/s", "ms_per_step": fb_ms,
+                           "workload": WORKLOADS["diff"][0] + "; loss = sum d^2, grads to points and vertices"}
+    else:
+        line["e2e"] = None
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(mesh, q)
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

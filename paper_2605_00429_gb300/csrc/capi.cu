@@ -72,15 +72,6 @@ static double now_ms() {
 
 using namespace p2m;
 
-struct p2m_index {
-    p2m_build_params params{};
-    std::vector<std::unique_ptr<MeshData>> meshes;
-    DevBuf status;          // device status word (ST_* bits)
-    DevBuf scratch_idx;     // out-of-domain query list
-    DevBuf scratch_cnt;
-    BatchState batch;       // batched-query state (tile queue, graph)
-    int device = 0;
-};
 
 namespace p2m {
 
@@ -101,6 +92,11 @@ int check_status_word(p2m_index* h, cudaStream_t s, const char* what) {
 }
 
 }  // namespace p2m
+
+p2m_index::~p2m_index() {
+    for (auto& st : streams)
+        if (st) cudaStreamDestroy(st);
+}
 
 // ----------------------------------------------------------------------------- validation
 
@@ -274,7 +270,8 @@ int p2m_query(p2m_index* h, const float* d_pts, int64_t n, float* d_dist, float*
     if (n < 0) return fail(P2M_ERR_INVALID_ARG, "n < 0");
     if (n == 0) return P2M_OK;
     if (!d_pts || !d_dist) return fail(P2M_ERR_INVALID_ARG, "d_pts and d_dist must be non-NULL");
-    return run_query(h, *h->meshes[0], d_pts, n, d_dist, d_closest, d_tri, d_bary, nullptr, (cudaStream_t)stream);
+    return run_query(h, *h->meshes[0], d_pts, n, d_dist, d_closest, d_tri, d_bary, nullptr, h->scratch_idx,
+                     (cudaStream_t)stream);
 }
 
 int p2m_query_counters(p2m_index* h, const float* d_pts, int64_t n, float* d_dist, p2m_counters* out,
@@ -292,7 +289,8 @@ int p2m_query_counters(p2m_index* h, const float* d_pts, int64_t n, float* d_dis
         P2M_TRY(dist.alloc(sizeof(float) * n));
         dd = dist.as<float>();
     }
-    P2M_TRY(run_query(h, *h->meshes[0], d_pts, n, dd, nullptr, nullptr, nullptr, cnt.as<unsigned long long>(), s));
+    P2M_TRY(run_query(h, *h->meshes[0], d_pts, n, dd, nullptr, nullptr, nullptr, cnt.as<unsigned long long>(),
+                      h->scratch_idx, s));
     unsigned long long c[8];
     P2M_CUDA_TRY(cudaMemcpyAsync(c, cnt.p, sizeof(c), cudaMemcpyDeviceToHost, s));
     P2M_CUDA_TRY(cudaStreamSynchronize(s));
@@ -392,12 +390,6 @@ int p2m_get_balls(const p2m_index* h, int mesh, int64_t* h_ball_offsets, double*
 
 // ----------------------------------------------------------------------------- not yet built
 extern "C" {
-int p2m_query_host(p2m_index*, const float*, int64_t, float*, float*, int32_t*, float*, void*) {
-    return fail(P2M_ERR_NOT_IMPLEMENTED, "p2m_query_host");
-}
-int p2m_backward(p2m_index*, const float*, int64_t, const int32_t*, const float*, const float*, float*, float*, void*) {
-    return fail(P2M_ERR_NOT_IMPLEMENTED, "p2m_backward");
-}
 int p2m_update_vertices(p2m_index*, const float*, void*) { return fail(P2M_ERR_NOT_IMPLEMENTED, "p2m_update_vertices"); }
 int p2m_batch_build(int, const float* const*, const int64_t*, const int32_t* const*, const int64_t*,
                     const p2m_build_params*, void*, p2m_index** out) {

@@ -3,6 +3,9 @@
 
 #include <cuda_runtime.h>
 
+#include <memory>
+#include <vector>
+
 #include "p2m_internal.h"
 
 struct p2m_index;
@@ -24,6 +27,26 @@ struct BatchState {
     ~BatchState() { if (exec) cudaGraphExecDestroy(exec); }
 };
 
+}  // namespace p2m
+
+// The index object behind the opaque C handle.
+struct p2m_index {
+    p2m_build_params params{};
+    std::vector<std::unique_ptr<p2m::MeshData>> meshes;
+    p2m::DevBuf status;        // device status word (ST_* bits)
+    p2m::DevBuf scratch_idx;   // compacted list of queries left to the BVH search
+    p2m::BatchState batch;     // batched-query state (tile queue, graph)
+    int device = 0;
+    // host-buffer query pipeline: two streams, each with its own device buffers
+    cudaStream_t streams[2] = {nullptr, nullptr};
+    p2m::DevBuf pipe[2][5];    // pts, dist, closest, tri, bary
+    p2m::DevBuf pipe_rest[2];
+    p2m::DevBuf grad_acc;      // fixed-point vertex-gradient accumulator
+    ~p2m_index();
+};
+
+namespace p2m {
+
 unsigned* index_status(p2m_index* h);
 DevBuf& index_rest(p2m_index* h);  // scratch for the compacted out-of-domain query list
 int check_status_word(p2m_index* h, cudaStream_t s, const char* what);
@@ -33,7 +56,7 @@ int build_partition(MeshData& m, const p2m_build_params& prm, p2m_index* h, cuda
 
 // Full query of one mesh; counters (8 x u64, may be NULL) accumulate instrumentation.
 int run_query(p2m_index* h, MeshData& m, const float* d_pts, int64_t n, float* d_dist, float* d_closest,
-              int32_t* d_tri, float* d_bary, unsigned long long* counters, cudaStream_t s);
+              int32_t* d_tri, float* d_bary, unsigned long long* counters, DevBuf& rest, cudaStream_t s);
 int run_nearest_site(p2m_index* h, MeshData& m, const float* d_pts, int64_t n, int32_t* d_site, cudaStream_t s);
 
 }  // namespace p2m

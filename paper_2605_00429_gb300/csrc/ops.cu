@@ -1,0 +1,144 @@
+// Host-buffer query pipeline and the backward kernel (K4).
+#include <algorithm>
+#include <cstring>
+
+#include "geom.cuh"
+#include "host.h"
+
+using namespace p2m;
+
+namespace p2m {
+
+// K4: gradient of sum_i g_i d(q_i, M) through the closest point p = sum_k b_k v_k of the
+// forward pass:  dd/dq = (q - p)/d,  dd/dv_k = -b_k (q - p)/d  (0 where d = 0).
+// Vertex sums either use float atomics, or 2^-32 fixed point in 64-bit integer atomics,
+// whose sum does not depend on the order of the additions (bit-reproducible).
+template <bool DET>
+__global__ void k_backward(const float* __restrict__ verts, const int32_t* __restrict__ tris,
+                           const float* __restrict__ pts, int64_t n, const int32_t* __restrict__ tri,
+                           const float* __restrict__ bary, const float* __restrict__ gdist, float* __restrict__ gpts,
+                           float* __restrict__ gverts, unsigned long long* __restrict__ gacc, int n_tris) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int f = tri[i];
+        const float3 q = make_float3(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]);
+        const float g = gdist[i];
+        if (f < 0 || f >= n_tris) {
+            if (gpts) { gpts[3 * i] = 0.f; gpts[3 * i + 1] = 0.f; gpts[3 * i + 2] = 0.f; }
+            continue;
+        }
+        const float b[3] = {bary[3 * i], bary[3 * i + 1], bary[3 * i + 2]};
+        int vi[3];
+        float3 p = make_float3(0.f, 0.f, 0.f);
+        for (int k = 0; k < 3; ++k) {
+            vi[k] = tris[3 * f + k];
+            p.x = fmaf(b[k], verts[3 * vi[k]], p.x);
+            p.y = fmaf(b[k], verts[3 * vi[k] + 1], p.y);
+            p.z = fmaf(b[k], verts[3 * vi[k] + 2], p.z);
+        }
+        const float3 d = q - p;
+        const float len = sqrtf(dot3(d, d));
+        const float s = len > 0.f ? g / len : 0.f;
+        const float3 u = s * d;  // g (q - p) / d
+        if (gpts) { gpts[3 * i] = u.x; gpts[3 * i + 1] = u.y; gpts[3 * i + 2] = u.z; }
+        if (gverts) {
+            for (int k = 0; k < 3; ++k) {
+                const float c[3] = {-b[k] * u.x, -b[k] * u.y, -b[k] * u.z};
+                for (int a = 0; a < 3; ++a) {
+                    if (DET) {
+                        const long long fx = __double2ll_rn((double)c[a] * 4294967296.0);
+                        atomicAdd(gacc + 3 * (int64_t)vi[k] + a, (unsigned long long)fx);
+                    } else {
+                        atomicAdd(gverts + 3 * (int64_t)vi[k] + a, c[a]);
+                    }
+                }
+            }
+        }
+    }
+}
+
+__global__ void k_fixed_to_float_add(const unsigned long long* __restrict__ acc, float* __restrict__ out, int64_t n) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+        out[i] += (float)((double)(long long)acc[i] * (1.0 / 4294967296.0));
+}
+
+}  // namespace p2m
+
+extern "C" {
+
+int p2m_backward(p2m_index* h, const float* d_pts, int64_t n, const int32_t* d_tri, const float* d_bary,
+                 const float* d_grad_dist, float* d_grad_pts, float* d_grad_verts, void* stream) {
+    if (!h || h->meshes.size() != 1) return fail(P2M_ERR_INVALID_ARG, "p2m_backward needs a single-mesh index");
+    if (n < 0) return fail(P2M_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return P2M_OK;
+    if (!d_pts || !d_tri || !d_bary || !d_grad_dist) return fail(P2M_ERR_INVALID_ARG, "NULL input");
+    cudaStream_t s = (cudaStream_t)stream;
+    MeshData& m = *h->meshes[0];
+    const int64_t nv3 = m.n_verts * 3;
+    const bool det = h->params.deterministic && d_grad_verts;
+    if (det) {
+        P2M_TRY(h->grad_acc.ensure(sizeof(unsigned long long) * nv3));
+        P2M_CUDA_TRY(cudaMemsetAsync(h->grad_acc.p, 0, sizeof(unsigned long long) * nv3, s));
+    }
+    const int threads = 256;
+    const int blocks = (int)std::min<int64_t>((n + threads - 1) / threads, 152 * 32);
+    if (det)
+        k_backward<true><<<blocks, threads, 0, s>>>(m.d_verts.as<float>(), m.d_tris.as<int32_t>(), d_pts, n, d_tri, d_bary,
+                                                     d_grad_dist, d_grad_pts, d_grad_verts,
+                                                     h->grad_acc.as<unsigned long long>(), (int)m.n_tris);
+    else
+        k_backward<false><<<blocks, threads, 0, s>>>(m.d_verts.as<float>(), m.d_tris.as<int32_t>(), d_pts, n, d_tri,
+                                                      d_bary, d_grad_dist, d_grad_pts, d_grad_verts, nullptr,
+                                                      (int)m.n_tris);
+    P2M_CUDA_TRY(cudaGetLastError());
+    if (det) {
+        k_fixed_to_float_add<<<(int)std::min<int64_t>((nv3 + 255) / 256, 4096), 256, 0, s>>>(
+            h->grad_acc.as<unsigned long long>(), d_grad_verts, nv3);
+        P2M_CUDA_TRY(cudaGetLastError());
+    }
+    return P2M_OK;
+}
+
+int p2m_query_host(p2m_index* h, const float* h_pts, int64_t n, float* h_dist, float* h_closest, int32_t* h_tri,
+                   float* h_bary, void* stream) {
+    if (!h || h->meshes.size() != 1) return fail(P2M_ERR_INVALID_ARG, "p2m_query_host needs a single-mesh index");
+    if (n < 0) return fail(P2M_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return P2M_OK;
+    if (!h_pts || !h_dist) return fail(P2M_ERR_INVALID_ARG, "h_pts and h_dist must be non-NULL");
+    MeshData& m = *h->meshes[0];
+    cudaStream_t user = (cudaStream_t)stream;
+    for (auto& st : h->streams)
+        if (!st) P2M_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    // the pipeline starts after the caller's earlier work on `stream`
+    cudaEvent_t ev;
+    P2M_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    P2M_CUDA_TRY(cudaEventRecord(ev, user));
+    for (auto& st : h->streams) P2M_CUDA_TRY(cudaStreamWaitEvent(st, ev, 0));
+    cudaEventDestroy(ev);
+    const int64_t chunk = std::min<int64_t>(n, (int64_t)1 << 21);
+    for (int k = 0; k < 2; ++k) {
+        P2M_TRY(h->pipe[k][0].ensure(sizeof(float) * 3 * chunk));
+        P2M_TRY(h->pipe[k][1].ensure(sizeof(float) * chunk));
+        if (h_closest) P2M_TRY(h->pipe[k][2].ensure(sizeof(float) * 3 * chunk));
+        if (h_tri) P2M_TRY(h->pipe[k][3].ensure(sizeof(int32_t) * chunk));
+        if (h_bary) P2M_TRY(h->pipe[k][4].ensure(sizeof(float) * 3 * chunk));
+    }
+    int slot = 0;
+    for (int64_t b = 0; b < n; b += chunk, slot ^= 1) {
+        const int64_t c = std::min(chunk, n - b);
+        cudaStream_t s = h->streams[slot];
+        DevBuf* P = h->pipe[slot];
+        P2M_CUDA_TRY(cudaMemcpyAsync(P[0].p, h_pts + 3 * b, sizeof(float) * 3 * c, cudaMemcpyHostToDevice, s));
+        P2M_TRY(run_query(h, m, P[0].as<float>(), c, P[1].as<float>(), h_closest ? P[2].as<float>() : nullptr,
+                          h_tri ? P[3].as<int32_t>() : nullptr, h_bary ? P[4].as<float>() : nullptr, nullptr,
+                          h->pipe_rest[slot], s));
+        P2M_CUDA_TRY(cudaMemcpyAsync(h_dist + b, P[1].p, sizeof(float) * c, cudaMemcpyDeviceToHost, s));
+        if (h_closest)
+            P2M_CUDA_TRY(cudaMemcpyAsync(h_closest + 3 * b, P[2].p, sizeof(float) * 3 * c, cudaMemcpyDeviceToHost, s));
+        if (h_tri) P2M_CUDA_TRY(cudaMemcpyAsync(h_tri + b, P[3].p, sizeof(int32_t) * c, cudaMemcpyDeviceToHost, s));
+        if (h_bary) P2M_CUDA_TRY(cudaMemcpyAsync(h_bary + 3 * b, P[4].p, sizeof(float) * 3 * c, cudaMemcpyDeviceToHost, s));
+    }
+    for (auto& st : h->streams) P2M_CUDA_TRY(cudaStreamSynchronize(st));
+    return check_status_word(h, h->streams[0], "query");
+}
+
+}  // extern "C"

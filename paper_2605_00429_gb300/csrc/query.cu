@@ -161,10 +161,9 @@ int query_grid_blocks(int64_t n, int threads) {
 }
 
 int run_query(p2m_index* h, MeshData& m, const float* d_pts, int64_t n, float* d_dist, float* d_closest,
-              int32_t* d_tri, float* d_bary, unsigned long long* counters, cudaStream_t s) {
+              int32_t* d_tri, float* d_bary, unsigned long long* counters, DevBuf& rest, cudaStream_t s) {
     const MeshView v = m.view();
     if (v.G == 0) return launch_bvh_closest(v, d_pts, nullptr, nullptr, n, d_dist, d_closest, d_tri, d_bary, index_status(h), s);
-    DevBuf& rest = index_rest(h);
     P2M_TRY(rest.ensure(sizeof(int32_t) * (n + 64)));
     int* n_rest = reinterpret_cast<int*>(rest.as<char>() + sizeof(int32_t) * (n + 32));
     P2M_CUDA_TRY(cudaMemsetAsync(n_rest, 0, sizeof(int), s));

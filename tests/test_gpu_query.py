@@ -37,16 +37,18 @@ def check_parity(mesh, q, out, ref=None):
     if ref is None:
         ref = oracle.closest(mesh.verts, mesh.tris, q)
     diag = mesh.diag()
-    tol = 1e-6 * diag
+    # 1e-6 diag; far outside the model (d > 4 diag) the FP32 output's own rounding
+    # (2 ulp = 2^-22 d) exceeds that, and bounds the error instead
+    tol = np.maximum(1e-6 * diag, 2.0 ** -22 * ref["dist"])
     err = np.abs(d.astype(np.float64) - ref["dist"])
-    assert np.max(err) <= tol, f"distance error {np.max(err):.3e} > {tol:.3e} at {np.argmax(err)}"
+    assert np.all(err <= tol), f"distance error {np.max(err - tol):.3e} above tolerance at {np.argmax(err - tol)}"
     tie = (ref["dist2"] - ref["dist"]) <= tol
     wrong = (t != ref["tri"]) & ~tie
     assert not wrong.any(), f"{wrong.sum()} triangle ids differ"
-    assert np.max(np.linalg.norm(c - ref["closest"], axis=1)[~tie], initial=0) <= 2 * tol
+    assert np.all((np.linalg.norm(c - ref["closest"], axis=1) <= 2 * tol) | tie)
     v = mesh.verts.astype(np.float64)
     p = np.einsum("nk,nkc->nc", b.astype(np.float64), v[mesh.tris[t]])
-    assert np.max(np.linalg.norm(p - c, axis=1)) <= 2 * tol
+    assert np.all(np.linalg.norm(p - c, axis=1) <= 2e-6 * diag)
     assert np.all(b >= -1e-5) and np.max(np.abs(b.sum(1) - 1)) < 1e-5
     return ref
 
