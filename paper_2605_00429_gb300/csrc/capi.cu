@@ -51,6 +51,9 @@ MeshView MeshData::view() const {
     v.refs = d_refs.as<const float4>();
     v.row_off = d_row_off.as<const int32_t>();
     v.row_tri = d_row_tri.as<const int32_t>();
+    v.chunk_off = d_chunk_off.as<const int32_t>();
+    v.cbox = d_cbox.as<const float4>();
+    v.long_row = long_row;
     v.cell_off = d_cell_off.as<const int32_t>();
     v.cell_site = d_cell_site.as<const int32_t>();
     v.G = G;
@@ -191,18 +194,20 @@ static int build_mesh(MeshData& m, const p2m_build_params& prm, p2m_index* h, cu
     st.ms_tri = t2 - t1;
     // K0: triangle LBVH
     {
-        DevBuf lo, hi;
-        P2M_TRY(lo.alloc(sizeof(float4) * T));
-        P2M_TRY(hi.alloc(sizeof(float4) * T));
-        P2M_TRY(tri_boxes(m.d_verts.as<float>(), m.d_tris.as<int32_t>(), T, lo.as<float4>(), hi.as<float4>(), s));
+        P2M_TRY(m.d_tlo.alloc(sizeof(float4) * T));
+        P2M_TRY(m.d_thi.alloc(sizeof(float4) * T));
+        P2M_TRY(tri_boxes(m.d_verts.as<float>(), m.d_tris.as<int32_t>(), T, m.d_tlo.as<float4>(), m.d_thi.as<float4>(), s));
         const float3 clo = make_float3((float)m.bb_lo[0], (float)m.bb_lo[1], (float)m.bb_lo[2]);
         const float3 chi = make_float3((float)m.bb_hi[0], (float)m.bb_hi[1], (float)m.bb_hi[2]);
-        P2M_TRY(build_lbvh(lo.as<float4>(), hi.as<float4>(), T, clo, chi, m.bvh, s));
+        P2M_TRY(build_lbvh(m.d_tlo.as<float4>(), m.d_thi.as<float4>(), T, clo, chi, m.bvh, s));
     }
     double t3 = now_ms();
     st.ms_lbvh = t3 - t2;
     // host Voronoi, augmentation, corner balls, lists, nearest-site grid
     P2M_TRY(build_partition(m, prm, h, s));
+    // list-scan schedule: 1 = thread per query for every list, 2 = warp per query for every
+    // list, 0/3 = thread per query for lists up to 64 entries and warp per query beyond
+    m.long_row = prm.schedule == 1 ? 0x7fffffff : (prm.schedule == 2 ? 0 : 64);
     st.ms_total = now_ms() - t0;
     return P2M_OK;
 }

@@ -10,6 +10,9 @@
 // (the traversal stack is warp-uniform); a node is entered if any lane's ball overlaps the
 // node box, a triangle is kept if any lane's ball reaches it.  Two passes share the code:
 // count, then (after a scan) fill.  Both passes visit triangles in the same order.
+#include <algorithm>
+#include <cmath>
+
 #include <cub/device/device_scan.cuh>
 
 #include "geom.cuh"
@@ -18,6 +21,7 @@
 namespace p2m {
 
 constexpr int kListWarps = 4;     // warps per block
+constexpr int kChunk = 32;        // list entries per chunk box
 constexpr int kListStack = 64;
 
 __device__ __forceinline__ bool any_ball_box(const float4* __restrict__ balls, int nb, float3 lo, float3 hi) {
@@ -112,6 +116,47 @@ __global__ void __launch_bounds__(32 * kListWarps) k_lists(const float4* __restr
     }
 }
 
+// Chunks of 32 consecutive list entries, each with the bounding box of its triangles
+// (grown by 2^-20 of the coordinate scale so that FP32 box distances stay lower bounds).
+// K1 emits each list in BVH order, so a chunk covers a compact patch of the mesh.
+__global__ void k_chunk_count(const int64_t* __restrict__ row_off64, int n_sites, int32_t* __restrict__ nch) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_sites; s += gridDim.x * blockDim.x)
+        nch[s] = (int32_t)((row_off64[s + 1] - row_off64[s] + kChunk - 1) / kChunk);
+}
+
+__global__ void k_chunk_boxes(const int64_t* __restrict__ row_off64, const int32_t* __restrict__ chunk_off, int n_sites,
+                              const int32_t* __restrict__ row_tri, const float4* __restrict__ tlo,
+                              const float4* __restrict__ thi, float pad, float4* __restrict__ cbox) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int s = warp; s < n_sites; s += nwarps) {
+        const int64_t r0 = row_off64[s], r1 = row_off64[s + 1];
+        const int c0 = chunk_off[s], nc = chunk_off[s + 1] - c0;
+        for (int k = 0; k < nc; ++k) {
+            const int64_t j = r0 + (int64_t)k * kChunk + lane;
+            float3 lo = make_float3(INFINITY, INFINITY, INFINITY), hi = make_float3(-INFINITY, -INFINITY, -INFINITY);
+            if (j < r1) {
+                const int f = row_tri[j];
+                lo = f3(tlo[f]);
+                hi = f3(thi[f]);
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                lo.x = fminf(lo.x, __shfl_xor_sync(0xffffffffu, lo.x, o));
+                lo.y = fminf(lo.y, __shfl_xor_sync(0xffffffffu, lo.y, o));
+                lo.z = fminf(lo.z, __shfl_xor_sync(0xffffffffu, lo.z, o));
+                hi.x = fmaxf(hi.x, __shfl_xor_sync(0xffffffffu, hi.x, o));
+                hi.y = fmaxf(hi.y, __shfl_xor_sync(0xffffffffu, hi.y, o));
+                hi.z = fmaxf(hi.z, __shfl_xor_sync(0xffffffffu, hi.z, o));
+            }
+            if (lane == 0) {
+                cbox[2 * (int64_t)(c0 + k)] = make_float4(lo.x - pad, lo.y - pad, lo.z - pad, 0.0f);
+                cbox[2 * (int64_t)(c0 + k) + 1] = make_float4(hi.x + pad, hi.y + pad, hi.z + pad, 0.0f);
+            }
+        }
+    }
+}
+
 __global__ void k_i64_to_i32(const int64_t* __restrict__ a, int32_t* __restrict__ b, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         b[i] = (int32_t)a[i];
@@ -147,6 +192,33 @@ int build_lists(MeshData& m, const float4* d_balls, const int64_t* d_ball_off, i
     P2M_CUDA_TRY(cudaGetLastError());
     k_i64_to_i32<<<64, 256, 0, s>>>(off64.as<int64_t>(), m.d_row_off.as<int32_t>(), n_sites + 1);
     P2M_CUDA_TRY(cudaGetLastError());
+    // chunk boxes
+    {
+        DevBuf nch;
+        P2M_TRY(nch.alloc(sizeof(int32_t) * (n_sites + 1)));
+        P2M_TRY(m.d_chunk_off.alloc(sizeof(int32_t) * (n_sites + 1)));
+        k_chunk_count<<<std::max(1, std::min((n_sites + 255) / 256, 4096)), 256, 0, s>>>(off64.as<int64_t>(), n_sites,
+                                                                                      nch.as<int32_t>());
+        P2M_CUDA_TRY(cudaGetLastError());
+        P2M_CUDA_TRY(cudaMemsetAsync(nch.as<int32_t>() + n_sites, 0, sizeof(int32_t), s));
+        size_t tb2 = 0;
+        P2M_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, tb2, nch.as<int32_t>(), m.d_chunk_off.as<int32_t>(), n_sites + 1, s));
+        DevBuf tmp2;
+        P2M_TRY(tmp2.alloc(tb2 + 16));
+        P2M_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp2.p, tb2, nch.as<int32_t>(), m.d_chunk_off.as<int32_t>(), n_sites + 1, s));
+        int32_t nc = 0;
+        P2M_CUDA_TRY(cudaMemcpyAsync(&nc, m.d_chunk_off.as<int32_t>() + n_sites, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        P2M_CUDA_TRY(cudaStreamSynchronize(s));
+        m.n_chunks = nc;
+        P2M_TRY(m.d_cbox.alloc(sizeof(float4) * 2 * std::max<int64_t>(nc, 1)));
+        double scale = m.diag;
+        for (int k = 0; k < 3; ++k) scale = std::max(scale, std::max(std::fabs(m.bb_lo[k]), std::fabs(m.bb_hi[k])));
+        const float pad = (float)(scale * std::ldexp(1.0, -20));
+        k_chunk_boxes<<<std::max(1, std::min((n_sites + 7) / 8, 152 * 16)), 256, 0, s>>>(
+            off64.as<int64_t>(), m.d_chunk_off.as<int32_t>(), n_sites, m.d_row_tri.as<int32_t>(), m.d_tlo.as<float4>(),
+            m.d_thi.as<float4>(), pad, m.d_cbox.as<float4>());
+        P2M_CUDA_TRY(cudaGetLastError());
+    }
     // row statistics (Table 1 Max / Avg)
     std::vector<int64_t> c(n_sites);
     P2M_CUDA_TRY(cudaMemcpyAsync(c.data(), cnt.p, sizeof(int64_t) * n_sites, cudaMemcpyDeviceToHost, s));

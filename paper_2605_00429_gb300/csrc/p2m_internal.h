@@ -83,6 +83,8 @@ struct MeshView {
     const float4* refs;     // [S] reference point on the mesh (x, y, z, rounding radius)
     const int32_t* row_off; // [S+1]
     const int32_t* row_tri; // [nnz]
+    const int32_t* chunk_off;  // [S+1] first 32-entry chunk of each list
+    const float4* cbox;     // [n_chunks][2] chunk bounding boxes (lo, hi)
     const int32_t* cell_off;// [G^3+1] nearest-site grid CSR
     const int32_t* cell_site;
     int G;                  // grid cells per axis (0 => no grid: every query takes the BVH path)
@@ -92,6 +94,7 @@ struct MeshView {
     float prune_abs;        // absolute prune slack
     int n_tris;
     int n_sites;
+    int long_row;           // lists longer than this go to the warp-per-query scan
 };
 
 struct MeshData {
@@ -109,10 +112,11 @@ struct MeshData {
     std::vector<double> ball_c;       // [B*3]
     std::vector<double> ball_r;       // [B]
     // device
-    DevBuf d_verts, d_tris, d_tri, d_tsph;
+    DevBuf d_verts, d_tris, d_tri, d_tsph, d_tlo, d_thi;
     Bvh bvh;
-    DevBuf d_sites, d_refs, d_row_off, d_row_tri, d_cell_off, d_cell_site;
-    int64_t nnz = 0;
+    DevBuf d_sites, d_refs, d_row_off, d_row_tri, d_cell_off, d_cell_site, d_chunk_off, d_cbox;
+    int64_t nnz = 0, n_chunks = 0;
+    int long_row = 64;
     int G = 0;
     float3 g_lo{}, g_hi{}, g_inv_h{};
     p2m_stats stats{};

@@ -67,37 +67,55 @@ __device__ __forceinline__ int nearest_site(const MeshView& m, float3 q, int cel
     return bs;
 }
 
-// Scan of one interception list; returns the (d2, tri) key and the (s, t) of the winner.
+constexpr int kChunk = 32;  // list entries per chunk box (matches the list build)
+
+__device__ __forceinline__ float ref_bound(const MeshView& m, float3 q, int site) {
+    const float4 ref = __ldg(m.refs + site);
+    const float rx = q.x - ref.x, ry = q.y - ref.y, rz = q.z - ref.z;
+    const float b = sqrtf(fmaf(rx, rx, fmaf(ry, ry, rz * rz))) + ref.w;
+    return fmaf(b, 1.0f + 9.6e-7f, m.prune_abs);
+}
+
+__device__ __forceinline__ bool chunk_may_hit(const MeshView& m, int c, float3 q, float bound) {
+    const float4 lo = __ldg(m.cbox + 2 * (int64_t)c), hi = __ldg(m.cbox + 2 * (int64_t)c + 1);
+    return box_dist2(q, f3(lo), f3(hi)) <= bound * bound;
+}
+
+// Thread scan of one interception list, chunk by chunk; returns the (d2, tri) key and the
+// (s, t) of the winner.
 template <bool COUNT>
 __device__ __forceinline__ unsigned long long scan_list(const MeshView& m, float3 q, int site, float& bs, float& bt,
                                                         unsigned long long* counters) {
     const int r0 = __ldg(m.row_off + site), r1 = __ldg(m.row_off + site + 1);
-    const float4 ref = __ldg(m.refs + site);
-    const float rx = q.x - ref.x, ry = q.y - ref.y, rz = q.z - ref.z;
-    float bound = sqrtf(fmaf(rx, rx, fmaf(ry, ry, rz * rz))) + ref.w;
-    bound = fmaf(bound, 1.0f + 9.6e-7f, m.prune_abs);
+    const int c0 = __ldg(m.chunk_off + site), c1 = __ldg(m.chunk_off + site + 1);
+    float bound = ref_bound(m, q, site);
     unsigned long long best = ~0ull;
-    int n_exact = 0;
-    for (int j = r0; j < r1; ++j) {
-        const int f = __ldg(m.row_tri + j);
-        const float4 sp = __ldg(m.tsph + f);
-        const float dx = q.x - sp.x, dy = q.y - sp.y, dz = q.z - sp.z;
-        const float lim = bound + sp.w;
-        if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) > lim * lim) continue;
-        if (COUNT) ++n_exact;
-        const TriRec T = load_tri(m.tri, f);
-        float s, t;
-        const float d2 = tri_dist2(q, T, s, t);
-        const unsigned long long key = dist_key(d2, f);
-        if (key < best) {
-            best = key;
-            bs = s;
-            bt = t;
-            bound = fminf(bound, fmaf(sqrtf(d2), 1.0f + 9.6e-7f, m.prune_abs));
+    int n_exact = 0, n_entries = 0;
+    for (int c = c0; c < c1; ++c) {
+        if (!chunk_may_hit(m, c, q, bound)) continue;
+        const int j0 = r0 + (c - c0) * kChunk, j1 = min(j0 + kChunk, r1);
+        if (COUNT) n_entries += j1 - j0;
+        for (int j = j0; j < j1; ++j) {
+            const int f = __ldg(m.row_tri + j);
+            const float4 sp = __ldg(m.tsph + f);
+            const float dx = q.x - sp.x, dy = q.y - sp.y, dz = q.z - sp.z;
+            const float lim = bound + sp.w;
+            if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) > lim * lim) continue;
+            if (COUNT) ++n_exact;
+            const TriRec T = load_tri(m.tri, f);
+            float s, t;
+            const float d2 = tri_dist2(q, T, s, t);
+            const unsigned long long key = dist_key(d2, f);
+            if (key < best) {
+                best = key;
+                bs = s;
+                bt = t;
+                bound = fminf(bound, fmaf(sqrtf(d2), 1.0f + 9.6e-7f, m.prune_abs));
+            }
         }
     }
     if (COUNT) {
-        atomicAdd(counters + C_ROWS, (unsigned long long)(r1 - r0));
+        atomicAdd(counters + C_ROWS, (unsigned long long)n_entries);
         atomicAdd(counters + C_EXACT, (unsigned long long)n_exact);
     }
     return best;
@@ -123,18 +141,24 @@ __device__ __forceinline__ void write_result(const MeshView& m, int64_t i, unsig
     }
 }
 
-// Thread-per-query schedule: fused nearest-site search and list scan.
+// Thread-per-query schedule: fused nearest-site search and list scan.  A query whose list
+// is longer than m.long_row is queued (query, site) for the warp-per-query scan.
 template <bool COUNT>
 __global__ void __launch_bounds__(256) k_query_thread(MeshView m, const float* __restrict__ pts, int64_t n,
                                                      float* __restrict__ dist, float* __restrict__ closest,
                                                      int32_t* __restrict__ tri_out, float* __restrict__ bary,
                                                      int32_t* __restrict__ rest, int* __restrict__ n_rest,
+                                                     int2* __restrict__ longq, int* __restrict__ n_long,
                                                      unsigned long long* counters) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float3 q = make_float3(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]);
         int cell;
         int site = -1;
         if (grid_cell(m, q, cell)) site = nearest_site<COUNT>(m, q, cell, counters);
+        if (site >= 0 && __ldg(m.row_off + site + 1) - __ldg(m.row_off + site) > m.long_row) {
+            longq[atomicAdd(n_long, 1)] = make_int2((int)i, site);
+            continue;
+        }
         unsigned long long key = ~0ull;
         float s = 0.0f, t = 0.0f;
         if (site >= 0) key = scan_list<COUNT>(m, q, site, s, t, counters);
@@ -144,6 +168,84 @@ __global__ void __launch_bounds__(256) k_query_thread(MeshView m, const float* _
             continue;
         }
         write_result(m, i, key, s, t, dist, closest, tri_out, bary);
+    }
+}
+
+// Warp-per-query schedule for long lists: lanes test 32 chunk boxes at once (ballot), then
+// the entries of each surviving chunk one per lane; the (d2, id) minimum is reduced across
+// the warp with two 32-bit redux operations and the bound shrinks after every chunk.
+template <bool COUNT>
+__global__ void __launch_bounds__(256) k_query_warp(MeshView m, const float* __restrict__ pts,
+                                                   const int2* __restrict__ longq, const int* __restrict__ n_long,
+                                                   float* __restrict__ dist, float* __restrict__ closest,
+                                                   int32_t* __restrict__ tri_out, float* __restrict__ bary,
+                                                   int32_t* __restrict__ rest, int* __restrict__ n_rest,
+                                                   unsigned long long* counters) {
+    const int lane = threadIdx.x & 31;
+    const int nq = *n_long;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nq; k += nwarps) {
+        const int2 qs = longq[k];
+        const int64_t i = qs.x;
+        const int site = qs.y;
+        const float3 q = make_float3(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]);
+        const int r0 = __ldg(m.row_off + site), r1 = __ldg(m.row_off + site + 1);
+        const int c0 = __ldg(m.chunk_off + site), nc = __ldg(m.chunk_off + site + 1) - c0;
+        float bound = ref_bound(m, q, site);
+        unsigned bhi = 0xffffffffu, blo = 0xffffffffu;  // best (d2 bits, id)
+        float bs = 0.0f, bt = 0.0f;
+        int n_exact = 0, n_entries = 0;
+        for (int cb = 0; cb < nc; cb += 32) {
+            const int ch = cb + lane;
+            unsigned mask = __ballot_sync(0xffffffffu, ch < nc && chunk_may_hit(m, c0 + ch, q, bound));
+            while (mask) {
+                const int kk = __ffs(mask) - 1;
+                mask &= mask - 1;
+                const int c = cb + kk;
+                if (!chunk_may_hit(m, c0 + c, q, bound)) continue;  // the bound may have shrunk
+                const int j = r0 + c * kChunk + lane;
+                unsigned khi = 0xffffffffu, klo = 0xffffffffu;
+                float s = 0.0f, t = 0.0f;
+                if (j < min(r0 + (c + 1) * kChunk, r1)) {
+                    if (COUNT) ++n_entries;
+                    const int f = __ldg(m.row_tri + j);
+                    const float4 sp = __ldg(m.tsph + f);
+                    const float dx = q.x - sp.x, dy = q.y - sp.y, dz = q.z - sp.z;
+                    const float lim = bound + sp.w;
+                    if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= lim * lim) {
+                        if (COUNT) ++n_exact;
+                        const TriRec T = load_tri(m.tri, f);
+                        const float d2 = tri_dist2(q, T, s, t);
+                        khi = __float_as_uint(d2);
+                        klo = (unsigned)f;
+                    }
+                }
+                const unsigned mhi = __reduce_min_sync(0xffffffffu, khi);
+                const unsigned mlo = __reduce_min_sync(0xffffffffu, khi == mhi ? klo : 0xffffffffu);
+                if (mhi < bhi || (mhi == bhi && mlo < blo)) {
+                    if (mhi != 0xffffffffu || mlo != 0xffffffffu) {
+                        const int owner = __ffs(__ballot_sync(0xffffffffu, khi == mhi && klo == mlo)) - 1;
+                        bs = __shfl_sync(0xffffffffu, s, owner);
+                        bt = __shfl_sync(0xffffffffu, t, owner);
+                        bhi = mhi;
+                        blo = mlo;
+                        bound = fminf(bound, fmaf(sqrtf(__uint_as_float(mhi)), 1.0f + 9.6e-7f, m.prune_abs));
+                    }
+                }
+            }
+        }
+        if (COUNT) {
+            atomicAdd(counters + C_ROWS, (unsigned long long)n_entries);
+            atomicAdd(counters + C_EXACT, (unsigned long long)n_exact);
+        }
+        if (lane == 0) {
+            if (bhi == 0xffffffffu && blo == 0xffffffffu) {
+                rest[atomicAdd(n_rest, 1)] = (int32_t)i;
+            } else {
+                const unsigned long long key = ((unsigned long long)bhi << 32) | blo;
+                write_result(m, i, key, bs, bt, dist, closest, tri_out, bary);
+            }
+        }
     }
 }
 
@@ -164,20 +266,31 @@ int run_query(p2m_index* h, MeshData& m, const float* d_pts, int64_t n, float* d
               int32_t* d_tri, float* d_bary, unsigned long long* counters, DevBuf& rest, cudaStream_t s) {
     const MeshView v = m.view();
     if (v.G == 0) return launch_bvh_closest(v, d_pts, nullptr, nullptr, n, d_dist, d_closest, d_tri, d_bary, index_status(h), s);
-    P2M_TRY(rest.ensure(sizeof(int32_t) * (n + 64)));
-    int* n_rest = reinterpret_cast<int*>(rest.as<char>() + sizeof(int32_t) * (n + 32));
-    P2M_CUDA_TRY(cudaMemsetAsync(n_rest, 0, sizeof(int), s));
+    // scratch: rest ids [n], long queue [n] of int2, two counters
+    const size_t rest_bytes = ((sizeof(int32_t) * n + 255) / 256) * 256;
+    const size_t long_bytes = ((sizeof(int2) * n + 255) / 256) * 256;
+    P2M_TRY(rest.ensure(rest_bytes + long_bytes + 256));
+    int32_t* d_rest = rest.as<int32_t>();
+    int2* d_long = reinterpret_cast<int2*>(rest.as<char>() + rest_bytes);
+    int* d_cnt = reinterpret_cast<int*>(rest.as<char>() + rest_bytes + long_bytes);
+    P2M_CUDA_TRY(cudaMemsetAsync(d_cnt, 0, 2 * sizeof(int), s));
     const int threads = 256;
     const int blocks = query_grid_blocks(n, threads);
-    if (counters)
-        k_query_thread<true><<<blocks, threads, 0, s>>>(v, d_pts, n, d_dist, d_closest, d_tri, d_bary, rest.as<int32_t>(),
-                                                        n_rest, counters);
-    else
-        k_query_thread<false><<<blocks, threads, 0, s>>>(v, d_pts, n, d_dist, d_closest, d_tri, d_bary, rest.as<int32_t>(),
-                                                         n_rest, nullptr);
+    const int wblocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, 152LL * 16));
+    if (counters) {
+        k_query_thread<true><<<blocks, threads, 0, s>>>(v, d_pts, n, d_dist, d_closest, d_tri, d_bary, d_rest, d_cnt,
+                                                        d_long, d_cnt + 1, counters);
+        k_query_warp<true><<<wblocks, threads, 0, s>>>(v, d_pts, d_long, d_cnt + 1, d_dist, d_closest, d_tri, d_bary,
+                                                       d_rest, d_cnt, counters);
+    } else {
+        k_query_thread<false><<<blocks, threads, 0, s>>>(v, d_pts, n, d_dist, d_closest, d_tri, d_bary, d_rest, d_cnt,
+                                                         d_long, d_cnt + 1, nullptr);
+        k_query_warp<false><<<wblocks, threads, 0, s>>>(v, d_pts, d_long, d_cnt + 1, d_dist, d_closest, d_tri, d_bary,
+                                                        d_rest, d_cnt, nullptr);
+    }
     P2M_CUDA_TRY(cudaGetLastError());
     // the points left over take the exact BVH search; the count stays on the device
-    return launch_bvh_closest(v, d_pts, rest.as<int32_t>(), n_rest, n, d_dist, d_closest, d_tri, d_bary, index_status(h), s);
+    return launch_bvh_closest(v, d_pts, d_rest, d_cnt, n, d_dist, d_closest, d_tri, d_bary, index_status(h), s);
 }
 
 int run_nearest_site(p2m_index* h, MeshData& m, const float* d_pts, int64_t n, int32_t* d_site, cudaStream_t s) {

@@ -167,3 +167,13 @@ def test_counters(p2m):
     c = idx.counters(torch.from_numpy(q).cuda())
     assert c["n_queries"] == 20000 and c["row_entries"] >= c["exact_tests"] > 0
     assert c["site_candidates"] >= 20000 - c["n_outside"]
+
+
+@pytest.mark.parametrize("schedule", [1, 2, 3])
+def test_schedules_agree(p2m, schedule):
+    """Thread-per-query, warp-per-query and the mixed schedule give the same answers."""
+    mesh, q = W.workload_large(50_000, k=4)
+    base = _query(p2m.P2MIndex(mesh.verts, mesh.tris, schedule=0), q)
+    other = _query(p2m.P2MIndex(mesh.verts, mesh.tris, schedule=schedule), q)
+    assert np.array_equal(base[0], other[0]) and np.array_equal(base[2], other[2])
+    check_parity(mesh, q[:5000], tuple(a[:5000] for a in other))
