@@ -229,6 +229,29 @@ int p2m_get_lists(const p2m_index* h, int mesh, int64_t* h_offsets, int32_t* h_t
 int p2m_get_balls(const p2m_index* h, int mesh, int64_t* h_ball_offsets, double* h_centres,
                   double* h_radii);
 
+/* ---- Allocation-free query.  The paper has no counterpart: this is a service entry
+ * point for callers that must not allocate device memory. --------------------------------
+ *
+ * Some callers cannot let a library call cudaMalloc / cudaFree: a framework that owns all
+ * device memory through its own pool or arena, a latency-bound loop that cannot afford the
+ * device-wide synchronisation those calls imply, or an operator hook that is forbidden to
+ * allocate.  p2m_query may grow a scratch buffer of the index on demand; this variant gives
+ * the same results as p2m_query (same arguments and outputs) but runs on a fixed scratch
+ * array compiled into the library: about 3 MiB of device memory on every GPU where the
+ * library is loaded, held until the process exits.  It calls no allocating routine.
+ *   * At most P2M_NOALLOC_MAX_QUERIES points per call; a larger n returns P2M_ERR_LIMIT
+ *     (split the batch).  The index itself must already exist (p2m_build allocates).
+ *   * The first call on each device looks up the scratch array's device address
+ *     (cudaGetSymbolAddress) with that device current; make that first call before any
+ *     stream capture begins.
+ *   * Every call on a device shares the one scratch array, and each call resets the parts
+ *     that must start at zero.  Calls whose work overlaps on the GPU (different streams, or
+ *     other host threads, without ordering between them) race on that array: order them.
+ * Asynchronous on `stream`.  Errors: INVALID_ARG, LIMIT, CUDA. */
+#define P2M_NOALLOC_MAX_QUERIES 262144
+int p2m_query_noalloc(p2m_index* h, const float* d_pts, int64_t n, float* d_dist, float* d_closest,
+                      int32_t* d_tri, float* d_bary, void* stream);
+
 /* ---- Host-only stage (no GPU needed). ------------------------------------------------ */
 
 /* The clipped Voronoi cells of a point set exactly as p2m_build computes them (Section 3.3:

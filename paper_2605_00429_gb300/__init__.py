@@ -82,7 +82,9 @@ SIGNATURES = {
     "p2m_get_lists": ([_P, _I, _P, _P], _I),
     "p2m_get_balls": ([_P, _I, _P, _P, _P], _I),
     "p2m_voronoi_cells": ([_P, _I64, _P, _P, _I, _P, _P, _P, _P], _I),
+    "p2m_query_noalloc": ([_P, _P, _I64, _P, _P, _P, _P, _P], _I),
 }
+NOALLOC_MAX_QUERIES = 262144
 
 
 def lib():

@@ -303,3 +303,25 @@ int run_nearest_site(p2m_index* h, MeshData& m, const float* d_pts, int64_t n, i
 }
 
 }  // namespace p2m
+
+namespace p2m {
+
+// The same launch sequence as run_query, on scratch memory the caller provides: d_rest
+// holds n int32, d_long n int2, d_cnt two ints.  Nothing is allocated here.
+int launch_query_on_scratch(p2m_index* h, MeshData& m, const float* d_pts, int64_t n, float* d_dist, float* d_closest,
+                            int32_t* d_tri, float* d_bary, int32_t* d_rest, int2* d_long, int* d_cnt, cudaStream_t s) {
+    const MeshView v = m.view();
+    if (v.G == 0) return launch_bvh_closest(v, d_pts, nullptr, nullptr, n, d_dist, d_closest, d_tri, d_bary, index_status(h), s);
+    P2M_CUDA_TRY(cudaMemsetAsync(d_cnt, 0, 2 * sizeof(int), s));
+    const int threads = 256;
+    const int blocks = query_grid_blocks(n, threads);
+    const int wblocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, 152LL * 16));
+    k_query_thread<false><<<blocks, threads, 0, s>>>(v, d_pts, n, d_dist, d_closest, d_tri, d_bary, d_rest, d_cnt, d_long,
+                                                     d_cnt + 1, nullptr);
+    k_query_warp<false><<<wblocks, threads, 0, s>>>(v, d_pts, d_long, d_cnt + 1, d_dist, d_closest, d_tri, d_bary, d_rest,
+                                                    d_cnt, nullptr);
+    P2M_CUDA_TRY(cudaGetLastError());
+    return launch_bvh_closest(v, d_pts, d_rest, d_cnt, n, d_dist, d_closest, d_tri, d_bary, index_status(h), s);
+}
+
+}  // namespace p2m
