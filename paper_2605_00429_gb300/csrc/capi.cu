@@ -1,7 +1,9 @@
 // C ABI of libp2mpp.so: argument checking, index lifecycle, build orchestration and query
 // dispatch.  The compute lives in the kernels of bvh.cu / lists.cu / grid.cu / query.cu and
 // the host Voronoi code of voronoi.cpp.
+#include <atomic>
 #include <chrono>
+#include <thread>
 #include <cmath>
 #include <cstring>
 #include <memory>
@@ -11,6 +13,7 @@
 
 #include "host.h"
 #include "p2m_internal.h"
+#include "voronoi.h"
 
 namespace p2m {
 
@@ -393,15 +396,82 @@ int p2m_get_balls(const p2m_index* h, int mesh, int64_t* h_ball_offsets, double*
 
 }  // extern "C"
 
-// ----------------------------------------------------------------------------- not yet built
+// ----------------------------------------------------------------------------- batch and update
+
 extern "C" {
-int p2m_update_vertices(p2m_index*, const float*, void*) { return fail(P2M_ERR_NOT_IMPLEMENTED, "p2m_update_vertices"); }
-int p2m_batch_build(int, const float* const*, const int64_t*, const int32_t* const*, const int64_t*,
-                    const p2m_build_params*, void*, p2m_index** out) {
-    if (out) *out = nullptr;
-    return fail(P2M_ERR_NOT_IMPLEMENTED, "p2m_batch_build");
+
+int p2m_batch_build(int n_meshes, const float* const* verts, const int64_t* n_verts, const int32_t* const* tris,
+                    const int64_t* n_tris, const p2m_build_params* params, void* stream, p2m_index** out) {
+    std::unique_ptr<p2m_index> h;
+    P2M_TRY(new_index(params, out, h));
+    if (n_meshes <= 0 || !verts || !n_verts || !tris || !n_tris)
+        return fail(P2M_ERR_INVALID_ARG, "batch needs n_meshes > 0 and non-NULL arrays");
+    h->meshes.resize(n_meshes);
+    for (int i = 0; i < n_meshes; ++i) {
+        h->meshes[i].reset(new MeshData());
+        const int rc = load_mesh(verts[i], n_verts[i], tris[i], n_tris[i], 0, *h->meshes[i]);
+        if (rc != P2M_OK) return fail(rc, "mesh " + std::to_string(i) + ": " + p2m_last_error());
+    }
+    // meshes build concurrently: each worker thread has its own stream and status word
+    std::atomic<int> next(0), err_mesh(-1);
+    std::mutex mu;
+    std::string err_msg;
+    int err_code = P2M_OK;
+    const int n_workers = std::max(1, std::min(n_meshes, std::max(2, hardware_threads() / 2)));
+    auto work = [&]() {
+        cudaSetDevice(h->device);
+        cudaStream_t ws = nullptr;
+        if (cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking) != cudaSuccess) return;
+        p2m_index local;
+        local.params = h->params;
+        local.device = h->device;
+        if (local.status.alloc(sizeof(unsigned) * 4) == P2M_OK) cudaMemset(local.status.p, 0, sizeof(unsigned) * 4);
+        while (err_mesh.load() < 0) {
+            const int i = next.fetch_add(1);
+            if (i >= n_meshes) break;
+            int rc = build_mesh(*h->meshes[i], h->params, &local, ws);
+            if (rc == P2M_OK) rc = check_status_word(&local, ws, "build");
+            if (rc != P2M_OK) {
+                std::lock_guard<std::mutex> lock(mu);
+                if (err_mesh.load() < 0) {
+                    err_mesh = i;
+                    err_code = rc;
+                    err_msg = p2m_last_error();
+                }
+            }
+        }
+        cudaStreamSynchronize(ws);
+        cudaStreamDestroy(ws);
+    };
+    std::vector<std::thread> th;
+    for (int t = 0; t < n_workers; ++t) th.emplace_back(work);
+    for (auto& t : th) t.join();
+    if (err_mesh.load() >= 0) return fail(err_code, "mesh " + std::to_string(err_mesh.load()) + ": " + err_msg);
+    P2M_CUDA_TRY(cudaStreamSynchronize((cudaStream_t)stream));
+    *out = h.release();
+    return P2M_OK;
 }
-int p2m_batch_query(p2m_index*, const float*, const int64_t*, float*, float*, int32_t*, float*, int, int, void*) {
-    return fail(P2M_ERR_NOT_IMPLEMENTED, "p2m_batch_query");
+
+int p2m_batch_query(p2m_index* batch, const float* d_pts, const int64_t* h_q_offsets, float* d_dist, float* d_closest,
+                    int32_t* d_tri, float* d_bary, int mode, int use_graph, void* stream) {
+    if (!batch || batch->meshes.empty() || !h_q_offsets) return fail(P2M_ERR_INVALID_ARG, "bad batch or offsets");
+    return run_batch_query(batch, d_pts, h_q_offsets, d_dist, d_closest, d_tri, d_bary, mode, use_graph,
+                           (cudaStream_t)stream);
 }
+
+int p2m_update_vertices(p2m_index* h, const float* d_verts, void* stream) {
+    if (!h || h->meshes.size() != 1 || !d_verts) return fail(P2M_ERR_INVALID_ARG, "p2m_update_vertices needs a single-mesh index");
+    cudaStream_t s = (cudaStream_t)stream;
+    MeshData& old = *h->meshes[0];
+    std::vector<float> v(old.n_verts * 3);
+    P2M_CUDA_TRY(cudaStreamSynchronize(s));
+    P2M_CUDA_TRY(cudaMemcpy(v.data(), d_verts, sizeof(float) * v.size(), cudaMemcpyDeviceToHost));
+    std::unique_ptr<MeshData> m(new MeshData());
+    P2M_TRY(load_mesh(v.data(), old.n_verts, old.tris.data(), old.n_tris, 0, *m));
+    P2M_TRY(build_mesh(*m, h->params, h, s));
+    P2M_TRY(check_status_word(h, s, "update_vertices"));
+    h->meshes[0] = std::move(m);
+    return P2M_OK;
 }
+
+}  // extern "C"

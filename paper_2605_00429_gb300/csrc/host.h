@@ -16,15 +16,23 @@ namespace p2m {
 struct BatchState {
     DevBuf views;        // MeshView per mesh (device copy)
     DevBuf tiles;        // int4 work list: (mesh, q_begin, q_end, 0)
-    DevBuf counter;      // tile queue head
+    DevBuf counter;      // tile head, long count, rest count, long head
+    DevBuf longq, rest;  // queues of the warp pass and of the BVH pass
     int n_tiles = 0;
     int tile = 0;        // queries per tile picked by the autotuner
-    int schedule = 0;    // 1 thread / 2 warp per query
+    int long_row = 64;   // lists longer than this take the warp-per-query pass
+    bool tuned = false;
+    float tune_ms = 0.f;
+    int grid_thread = 0, grid_warp = 0, grid_bvh = 0;
     std::vector<int64_t> offsets;  // host offsets the work list was built for
     const void* graph_pts = nullptr;
     const void* graph_out[4] = {nullptr, nullptr, nullptr, nullptr};
     cudaGraphExec_t exec = nullptr;
-    ~BatchState() { if (exec) cudaGraphExecDestroy(exec); }
+    cudaStream_t cap = nullptr;  // private stream the graph is captured on
+    ~BatchState() {
+        if (exec) cudaGraphExecDestroy(exec);
+        if (cap) cudaStreamDestroy(cap);
+    }
 };
 
 }  // namespace p2m
@@ -58,5 +66,7 @@ int build_partition(MeshData& m, const p2m_build_params& prm, p2m_index* h, cuda
 int run_query(p2m_index* h, MeshData& m, const float* d_pts, int64_t n, float* d_dist, float* d_closest,
               int32_t* d_tri, float* d_bary, unsigned long long* counters, DevBuf& rest, cudaStream_t s);
 int run_nearest_site(p2m_index* h, MeshData& m, const float* d_pts, int64_t n, int32_t* d_site, cudaStream_t s);
+int run_batch_query(p2m_index* h, const float* d_pts, const int64_t* h_off, float* d_dist, float* d_closest,
+                    int32_t* d_tri, float* d_bary, int mode, int use_graph, cudaStream_t s);
 
 }  // namespace p2m
