@@ -62,7 +62,7 @@ __global__ void __launch_bounds__(256) k_batch_thread(BatchArgs a) {
     }
 }
 
-__global__ void __launch_bounds__(256) k_batch_warp(BatchArgs a) {
+__global__ void __launch_bounds__(256, 2) k_batch_warp(BatchArgs a) {
     const int lane = threadIdx.x & 31;
     const int nq = *(volatile int*)(a.ctr + 1);
     while (true) {

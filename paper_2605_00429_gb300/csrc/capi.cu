@@ -56,6 +56,8 @@ MeshView MeshData::view() const {
     v.row_tri = d_row_tri.as<const int32_t>();
     v.chunk_off = d_chunk_off.as<const int32_t>();
     v.cbox = d_cbox.as<const float4>();
+    v.l1_off = d_l1_off.as<const int32_t>();
+    v.l1box = d_l1box.as<const float4>();
     v.long_row = long_row;
     v.cell_off = d_cell_off.as<const int32_t>();
     v.cell_site = d_cell_site.as<const int32_t>();

@@ -126,7 +126,8 @@ __global__ void k_chunk_count(const int64_t* __restrict__ row_off64, int n_sites
 
 __global__ void k_chunk_boxes(const int64_t* __restrict__ row_off64, const int32_t* __restrict__ chunk_off, int n_sites,
                               const int32_t* __restrict__ row_tri, const float4* __restrict__ tlo,
-                              const float4* __restrict__ thi, float pad, float4* __restrict__ cbox) {
+                              const float4* __restrict__ thi, const float4* __restrict__ tri, float pad,
+                              float4* __restrict__ cbox) {
     const int lane = threadIdx.x & 31;
     const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
     const int nwarps = (gridDim.x * blockDim.x) >> 5;
@@ -136,10 +137,70 @@ __global__ void k_chunk_boxes(const int64_t* __restrict__ row_off64, const int32
         for (int k = 0; k < nc; ++k) {
             const int64_t j = r0 + (int64_t)k * kChunk + lane;
             float3 lo = make_float3(INFINITY, INFINITY, INFINITY), hi = make_float3(-INFINITY, -INFINITY, -INFINITY);
+            float3 nsum = make_float3(0.f, 0.f, 0.f);
+            int f = -1;
             if (j < r1) {
-                const int f = row_tri[j];
+                f = row_tri[j];
                 lo = f3(tlo[f]);
                 hi = f3(thi[f]);
+                nsum = f3(tri[4 * (int64_t)f + 3]);  // area-weighted normal (e0 x e1)
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                lo.x = fminf(lo.x, __shfl_xor_sync(0xffffffffu, lo.x, o));
+                lo.y = fminf(lo.y, __shfl_xor_sync(0xffffffffu, lo.y, o));
+                lo.z = fminf(lo.z, __shfl_xor_sync(0xffffffffu, lo.z, o));
+                hi.x = fmaxf(hi.x, __shfl_xor_sync(0xffffffffu, hi.x, o));
+                hi.y = fmaxf(hi.y, __shfl_xor_sync(0xffffffffu, hi.y, o));
+                hi.z = fmaxf(hi.z, __shfl_xor_sync(0xffffffffu, hi.z, o));
+                nsum.x += __shfl_xor_sync(0xffffffffu, nsum.x, o);
+                nsum.y += __shfl_xor_sync(0xffffffffu, nsum.y, o);
+                nsum.z += __shfl_xor_sync(0xffffffffu, nsum.z, o);
+            }
+            // slab of the chunk along its mean normal: extent of n.v over its vertices
+            const float nl = sqrtf(dot3(nsum, nsum));
+            const float3 n = nl > 0.0f ? (1.0f / nl) * nsum : make_float3(0.f, 0.f, 0.f);
+            float hmin = INFINITY, hmax = -INFINITY;
+            if (f >= 0) {
+                const float4* r = tri + 4 * (int64_t)f;
+                const float3 v0 = f3(r[0]), e0 = f3(r[1]), e1 = f3(r[2]);
+                const float a = dot3(n, v0), b = dot3(n, e0), c = dot3(n, e1);
+                hmin = fminf(a, fminf(a + b, a + c));
+                hmax = fmaxf(a, fmaxf(a + b, a + c));
+            }
+            for (int o = 16; o > 0; o >>= 1) {
+                hmin = fminf(hmin, __shfl_xor_sync(0xffffffffu, hmin, o));
+                hmax = fmaxf(hmax, __shfl_xor_sync(0xffffffffu, hmax, o));
+            }
+            if (lane == 0) {
+                // a zero normal leaves the slab unbounded (then only the box prunes)
+                const bool ok = nl > 0.0f;
+                cbox[3 * (int64_t)(c0 + k)] = make_float4(lo.x - pad, lo.y - pad, lo.z - pad, ok ? hmin - 2.0f * pad : -INFINITY);
+                cbox[3 * (int64_t)(c0 + k) + 1] = make_float4(hi.x + pad, hi.y + pad, hi.z + pad, ok ? hmax + 2.0f * pad : INFINITY);
+                cbox[3 * (int64_t)(c0 + k) + 2] = make_float4(n.x, n.y, n.z, 0.0f);
+            }
+        }
+    }
+}
+
+// Level-1 boxes: the union of each run of 32 consecutive chunk boxes of a list.
+__global__ void k_count_parents(const int32_t* __restrict__ child_off, int n_sites, int32_t* __restrict__ npar) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_sites; s += gridDim.x * blockDim.x)
+        npar[s] = (child_off[s + 1] - child_off[s] + 31) / 32;
+}
+
+__global__ void k_parent_boxes(const int32_t* __restrict__ child_off, const int32_t* __restrict__ par_off, int n_sites,
+                               const float4* __restrict__ cbox, float4* __restrict__ pbox) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int s = warp; s < n_sites; s += nwarps) {
+        const int c0 = child_off[s], nc = child_off[s + 1] - c0, p0 = par_off[s];
+        for (int k = 0; 32 * k < nc; ++k) {
+            const int c = 32 * k + lane;
+            float3 lo = make_float3(INFINITY, INFINITY, INFINITY), hi = make_float3(-INFINITY, -INFINITY, -INFINITY);
+            if (c < nc) {
+                lo = f3(cbox[3 * (int64_t)(c0 + c)]);
+                hi = f3(cbox[3 * (int64_t)(c0 + c) + 1]);
             }
             for (int o = 16; o > 0; o >>= 1) {
                 lo.x = fminf(lo.x, __shfl_xor_sync(0xffffffffu, lo.x, o));
@@ -150,8 +211,8 @@ __global__ void k_chunk_boxes(const int64_t* __restrict__ row_off64, const int32
                 hi.z = fmaxf(hi.z, __shfl_xor_sync(0xffffffffu, hi.z, o));
             }
             if (lane == 0) {
-                cbox[2 * (int64_t)(c0 + k)] = make_float4(lo.x - pad, lo.y - pad, lo.z - pad, 0.0f);
-                cbox[2 * (int64_t)(c0 + k) + 1] = make_float4(hi.x + pad, hi.y + pad, hi.z + pad, 0.0f);
+                pbox[2 * (int64_t)(p0 + k)] = make_float4(lo.x, lo.y, lo.z, 0.0f);
+                pbox[2 * (int64_t)(p0 + k) + 1] = make_float4(hi.x, hi.y, hi.z, 0.0f);
             }
         }
     }
@@ -210,13 +271,27 @@ int build_lists(MeshData& m, const float4* d_balls, const int64_t* d_ball_off, i
         P2M_CUDA_TRY(cudaMemcpyAsync(&nc, m.d_chunk_off.as<int32_t>() + n_sites, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         P2M_CUDA_TRY(cudaStreamSynchronize(s));
         m.n_chunks = nc;
-        P2M_TRY(m.d_cbox.alloc(sizeof(float4) * 2 * std::max<int64_t>(nc, 1)));
+        P2M_TRY(m.d_cbox.alloc(sizeof(float4) * 3 * std::max<int64_t>(nc, 1)));
         double scale = m.diag;
         for (int k = 0; k < 3; ++k) scale = std::max(scale, std::max(std::fabs(m.bb_lo[k]), std::fabs(m.bb_hi[k])));
         const float pad = (float)(scale * std::ldexp(1.0, -20));
         k_chunk_boxes<<<std::max(1, std::min((n_sites + 7) / 8, 152 * 16)), 256, 0, s>>>(
             off64.as<int64_t>(), m.d_chunk_off.as<int32_t>(), n_sites, m.d_row_tri.as<int32_t>(), m.d_tlo.as<float4>(),
-            m.d_thi.as<float4>(), pad, m.d_cbox.as<float4>());
+            m.d_thi.as<float4>(), m.d_tri.as<float4>(), pad, m.d_cbox.as<float4>());
+        P2M_CUDA_TRY(cudaGetLastError());
+        // level-1 boxes over 32 chunks
+        P2M_TRY(m.d_l1_off.alloc(sizeof(int32_t) * (n_sites + 1)));
+        k_count_parents<<<std::max(1, std::min((n_sites + 255) / 256, 4096)), 256, 0, s>>>(m.d_chunk_off.as<int32_t>(),
+                                                                                        n_sites, nch.as<int32_t>());
+        P2M_CUDA_TRY(cudaGetLastError());
+        P2M_CUDA_TRY(cudaMemsetAsync(nch.as<int32_t>() + n_sites, 0, sizeof(int32_t), s));
+        P2M_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp2.p, tb2, nch.as<int32_t>(), m.d_l1_off.as<int32_t>(), n_sites + 1, s));
+        int32_t n1 = 0;
+        P2M_CUDA_TRY(cudaMemcpyAsync(&n1, m.d_l1_off.as<int32_t>() + n_sites, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
+        P2M_CUDA_TRY(cudaStreamSynchronize(s));
+        P2M_TRY(m.d_l1box.alloc(sizeof(float4) * 2 * std::max<int32_t>(n1, 1)));
+        k_parent_boxes<<<std::max(1, std::min((n_sites + 7) / 8, 152 * 16)), 256, 0, s>>>(
+            m.d_chunk_off.as<int32_t>(), m.d_l1_off.as<int32_t>(), n_sites, m.d_cbox.as<float4>(), m.d_l1box.as<float4>());
         P2M_CUDA_TRY(cudaGetLastError());
     }
     // row statistics (Table 1 Max / Avg)

@@ -84,7 +84,9 @@ struct MeshView {
     const int32_t* row_off; // [S+1]
     const int32_t* row_tri; // [nnz]
     const int32_t* chunk_off;  // [S+1] first 32-entry chunk of each list
-    const float4* cbox;     // [n_chunks][2] chunk bounding boxes (lo, hi)
+    const float4* cbox;     // [n_chunks][3] chunk bounds: (lo, hmin), (hi, hmax), (unit normal, 0)
+    const int32_t* l1_off;  // [S+1] first level-1 box (32 chunks = 1024 entries) of each list
+    const float4* l1box;    // [n_l1][2]
     const int32_t* cell_off;// [G^3+1] nearest-site grid CSR
     const int32_t* cell_site;
     int G;                  // grid cells per axis (0 => no grid: every query takes the BVH path)
@@ -114,7 +116,7 @@ struct MeshData {
     // device
     DevBuf d_verts, d_tris, d_tri, d_tsph, d_tlo, d_thi;
     Bvh bvh;
-    DevBuf d_sites, d_refs, d_row_off, d_row_tri, d_cell_off, d_cell_site, d_chunk_off, d_cbox;
+    DevBuf d_sites, d_refs, d_row_off, d_row_tri, d_cell_off, d_cell_site, d_chunk_off, d_cbox, d_l1_off, d_l1box;
     int64_t nnz = 0, n_chunks = 0;
     int long_row = 64;
     int G = 0;

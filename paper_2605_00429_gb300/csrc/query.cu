@@ -46,7 +46,7 @@ __global__ void __launch_bounds__(256) k_query_thread(MeshView m, const float* _
 
 // Warp-per-query schedule for the queued long lists.
 template <bool COUNT>
-__global__ void __launch_bounds__(256) k_query_warp(MeshView m, const float* __restrict__ pts,
+__global__ void __launch_bounds__(256, 2) k_query_warp(MeshView m, const float* __restrict__ pts,
                                                    const int2* __restrict__ longq, const int* __restrict__ n_long,
                                                    float* __restrict__ dist, float* __restrict__ closest,
                                                    int32_t* __restrict__ tri_out, float* __restrict__ bary,

@@ -69,9 +69,19 @@ __device__ __forceinline__ float ref_bound(const MeshView& m, float3 q, int site
     return fmaf(b, 1.0f + 9.6e-7f, m.prune_abs);
 }
 
+// Squared lower bound of the distance from q to the triangles of chunk c: the larger of the
+// distance to the chunk's box and the distance to its normal slab {x : hmin <= n.x <= hmax}
+// (n = the chunk's mean unit normal, hmin / hmax padded like the box).
+__device__ __forceinline__ float chunk_dist2(const MeshView& m, int c, float3 q) {
+    const float4* r = m.cbox + 3 * (int64_t)c;
+    const float4 lo = __ldg(r), hi = __ldg(r + 1), n = __ldg(r + 2);
+    const float h = dot3(f3(n), q);
+    const float slab = fmaxf(fmaxf(lo.w - h, h - hi.w), 0.0f);
+    return fmaxf(box_dist2(q, f3(lo), f3(hi)), slab * slab);
+}
+
 __device__ __forceinline__ bool chunk_may_hit(const MeshView& m, int c, float3 q, float bound) {
-    const float4 lo = __ldg(m.cbox + 2 * (int64_t)c), hi = __ldg(m.cbox + 2 * (int64_t)c + 1);
-    return box_dist2(q, f3(lo), f3(hi)) <= bound * bound;
+    return chunk_dist2(m, c, q) <= bound * bound;
 }
 
 // Thread scan of one interception list, chunk by chunk; returns the (d2, tri) key and the
@@ -134,57 +144,100 @@ __device__ __forceinline__ void write_result(const MeshView& m, int64_t i, unsig
     }
 }
 
-// Warp-cooperative scan of one long list (all 32 lanes call it with the same query): lanes
-// test 32 chunk boxes at once (ballot), then the entries of each surviving chunk one per
-// lane; the (d2, id) minimum is reduced across the warp with two 32-bit redux operations and
-// the bound shrinks after every chunk.  Returns false if no triangle was found.
+__device__ __forceinline__ float box2_dist2(const float4* __restrict__ box, int64_t k, float3 q) {
+    const float4 lo = __ldg(box + 2 * k), hi = __ldg(box + 2 * k + 1);
+    return box_dist2(q, f3(lo), f3(hi));
+}
+
+// Warp-cooperative, best-first scan of one long list (all 32 lanes call it with the same
+// query).  The list is a sequence of 32-entry chunks, and every 32 chunks have a level-1
+// box.  The warp first scans the level-1 box nearest to q, which makes the bound tight
+// early; it then visits level-1 boxes, and the chunks inside each, in ascending box
+// distance (selected with redux.sync + ballot), stopping at the bound.  Within a chunk the
+// entries go one per lane, and the (d2, id) minimum is reduced across the warp with two
+// 32-bit redux operations.  Anything skipped has a box farther than the bound at the time
+// of the test, and the bound only shrinks, so the result is the list's exact minimum.
+// Returns false if no triangle was found.
 template <bool COUNT>
 __device__ __forceinline__ bool warp_scan_list(const MeshView& m, float3 q, int site, unsigned& bhi, unsigned& blo,
                                                float& bs, float& bt, unsigned long long* counters) {
+    const unsigned FULL = 0xffffffffu;
     const int lane = threadIdx.x & 31;
     const int r0 = __ldg(m.row_off + site), r1 = __ldg(m.row_off + site + 1);
     const int c0 = __ldg(m.chunk_off + site), nc = __ldg(m.chunk_off + site + 1) - c0;
+    const int p0 = __ldg(m.l1_off + site), np = __ldg(m.l1_off + site + 1) - p0;
     float bound = ref_bound(m, q, site);
     bhi = 0xffffffffu;
     blo = 0xffffffffu;
     bs = 0.0f;
     bt = 0.0f;
     int n_exact = 0, n_entries = 0;
-    for (int cb = 0; cb < nc; cb += 32) {
-        const int ch = cb + lane;
-        unsigned mask = __ballot_sync(0xffffffffu, ch < nc && chunk_may_hit(m, c0 + ch, q, bound));
-        while (mask) {
-            const int kk = __ffs(mask) - 1;
-            mask &= mask - 1;
-            const int c = cb + kk;
-            if (!chunk_may_hit(m, c0 + c, q, bound)) continue;  // the bound may have shrunk
-            const int j = r0 + c * kChunk + lane;
-            unsigned khi = 0xffffffffu, klo = 0xffffffffu;
-            float s = 0.0f, t = 0.0f;
-            if (j < min(r0 + (c + 1) * kChunk, r1)) {
-                if (COUNT) ++n_entries;
-                const int f = __ldg(m.row_tri + j);
-                const float4 sp = __ldg(m.tsph + f);
-                const float dx = q.x - sp.x, dy = q.y - sp.y, dz = q.z - sp.z;
-                const float lim = bound + sp.w;
-                if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= lim * lim) {
-                    if (COUNT) ++n_exact;
-                    const TriRec T = load_tri(m.tri, f);
-                    const float d2 = tri_dist2(q, T, s, t);
-                    khi = __float_as_uint(d2);
-                    klo = (unsigned)f;
-                }
+
+    // entries of chunk c (warp-uniform), one per lane
+    auto do_chunk = [&](int c) {
+        const int j = r0 + c * kChunk + lane;
+        unsigned khi = 0xffffffffu, klo = 0xffffffffu;
+        float s = 0.0f, t = 0.0f;
+        if (j < min(r0 + (c + 1) * kChunk, r1)) {
+            if (COUNT) ++n_entries;
+            const int f = __ldg(m.row_tri + j);
+            const float4 sp = __ldg(m.tsph + f);
+            const float dx = q.x - sp.x, dy = q.y - sp.y, dz = q.z - sp.z;
+            const float lim = bound + sp.w;
+            if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= lim * lim) {
+                if (COUNT) ++n_exact;
+                const TriRec T = load_tri(m.tri, f);
+                const float d2 = tri_dist2(q, T, s, t);
+                khi = __float_as_uint(d2);
+                klo = (unsigned)f;
             }
-            const unsigned mhi = __reduce_min_sync(0xffffffffu, khi);
-            const unsigned mlo = __reduce_min_sync(0xffffffffu, khi == mhi ? klo : 0xffffffffu);
-            if ((mhi < bhi || (mhi == bhi && mlo < blo)) && (mhi != 0xffffffffu || mlo != 0xffffffffu)) {
-                const int owner = __ffs(__ballot_sync(0xffffffffu, khi == mhi && klo == mlo)) - 1;
-                bs = __shfl_sync(0xffffffffu, s, owner);
-                bt = __shfl_sync(0xffffffffu, t, owner);
-                bhi = mhi;
-                blo = mlo;
-                bound = fminf(bound, fmaf(sqrtf(__uint_as_float(mhi)), 1.0f + 9.6e-7f, m.prune_abs));
-            }
+        }
+        const unsigned mhi = __reduce_min_sync(FULL, khi);
+        const unsigned mlo = __reduce_min_sync(FULL, khi == mhi ? klo : 0xffffffffu);
+        if ((mhi < bhi || (mhi == bhi && mlo < blo)) && (mhi != 0xffffffffu || mlo != 0xffffffffu)) {
+            const int owner = __ffs(__ballot_sync(FULL, khi == mhi && klo == mlo)) - 1;
+            bs = __shfl_sync(FULL, s, owner);
+            bt = __shfl_sync(FULL, t, owner);
+            bhi = mhi;
+            blo = mlo;
+            bound = fminf(bound, fmaf(sqrtf(__uint_as_float(mhi)), 1.0f + 9.6e-7f, m.prune_abs));
+        }
+    };
+    // chunks of level-1 box p, nearest first
+    auto do_node = [&](int p) {
+        const int ch = 32 * p + lane;
+        const float d = ch < nc ? chunk_dist2(m, c0 + ch, q) : INFINITY;
+        bool live = d <= bound * bound;
+        while (__any_sync(FULL, live)) {
+            const unsigned dm = __reduce_min_sync(FULL, live ? __float_as_uint(d) : 0xffffffffu);
+            if (__uint_as_float(dm) > bound * bound) break;
+            const int owner = __ffs(__ballot_sync(FULL, live && __float_as_uint(d) == dm)) - 1;
+            if (lane == owner) live = false;
+            do_chunk(32 * p + owner);
+        }
+    };
+    // pre-pass: the nearest level-1 box
+    unsigned nd = 0xffffffffu, ni = 0xffffffffu;
+    for (int pb = 0; pb < np; pb += 32) {
+        const int p = pb + lane;
+        const unsigned d = p < np ? __float_as_uint(box2_dist2(m.l1box, p0 + p, q)) : 0xffffffffu;
+        const unsigned dmin = __reduce_min_sync(FULL, d);
+        const unsigned imin = __reduce_min_sync(FULL, d == dmin ? (unsigned)p : 0xffffffffu);
+        if (dmin < nd) { nd = dmin; ni = imin; }
+    }
+    const int first = (int)ni;
+    if (np > 0 && __uint_as_float(nd) <= bound * bound) do_node(first);
+    // the other level-1 boxes, nearest first within each group of 32
+    for (int pb = 0; pb < np; pb += 32) {
+        const int p = pb + lane;
+        const float d = (p < np && p != first) ? box2_dist2(m.l1box, p0 + p, q) : INFINITY;
+        bool live = d <= bound * bound;
+        while (__any_sync(FULL, live)) {
+            const unsigned dm = __reduce_min_sync(FULL, live ? __float_as_uint(d) : 0xffffffffu);
+            if (__uint_as_float(dm) > bound * bound) break;
+            const int owner = __ffs(__ballot_sync(FULL, live && __float_as_uint(d) == dm)) - 1;
+            if (lane == owner) live = false;
+            do_node(pb + owner);
         }
     }
     if (COUNT) {
