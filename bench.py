@@ -52,6 +52,26 @@ WORKLOADS = {
 }
 
 
+def reduce_max_ms(ms, world, device=None):
+    """Step time of the slowest rank (every rank calls this; world == 1 returns ms)."""
+    if world <= 1:
+        return ms
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([ms], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def replicas_value(n_per_rank, ms, world):
+    """Whole-job queries/s of `world` replicas that each answer n_per_rank queries per step."""
+    return world * n_per_rank / (ms / 1e3)
+
+
+def metric_name(config):
+    return "closest-point queries/s (10M pts, 82k tris)" if config == "large" else f"closest-point queries/s ({config})"
+
+
 def _env_int(name, default):
     try:
         return int(os.environ.get(name, default))
@@ -112,6 +132,26 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+def profiled_traffic(config, n):
+    """DRAM bytes per query pass from the committed ncu summary of this workload, scaled to n
+    queries, if the summary was taken on the current query-kernel sources (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", f"k_query_{config}.md")
+    srcs = [os.path.join(ROOT, "paper_2605_00429_gb300", "csrc", f) for f in ("query.cu", "query_dev.cuh", "geom.cuh")]
+    try:
+        h = hashlib.sha256(b"".join(open(f, "rb").read() for f in srcs)).hexdigest()[:16]
+        fields = {}
+        for line in open(path):
+            if ":" in line and line.startswith("- "):
+                k, v = line[2:].split(":", 1)
+                fields[k.strip()] = v.strip()
+        if fields.get("source_sha256_16") != h:
+            return None
+        return float(fields["dram_bytes_per_query"]) * n
+    except (OSError, KeyError, ValueError):
+        return None
+
+
 def cpu_baseline(mesh, q, target_s=12.0, seed=0):
     """The FP64 oracle (as it stands) on a bounded random sample of the workload's queries."""
     import oracle
@@ -155,7 +195,7 @@ def run_reference(args, rank, world):
             times.append(time.perf_counter() - t)
     ms = float(np.mean(times)) * 1e3
     value = n / (ms / 1e3)
-    line = {"impl": "reference", "metric": "closest-point queries/s", "value": value, "unit": "queries/s",
+    line = {"impl": "reference", "metric": metric_name(args.config), "value": value, "unit": "queries/s",
             "n_gpus": world, "steps": steps, "warmup": warm, "ms_per_step": ms, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": desc, "queries_per_step": n},
@@ -238,12 +278,8 @@ def main():
     barrier()
     clocks = sampler.stop()
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    ms = float(np.mean(step_ms))
-    if world > 1:
-        t = torch.tensor([ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * n / (ms / 1e3)
+    ms = reduce_max_ms(float(np.mean(step_ms)), world, dev)
+    value = replicas_value(n, ms, world)
 
     pk, pk_kind = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
@@ -253,15 +289,15 @@ def main():
     achieved = flops / (ms / 1e3) / 1e12
     hbm_gbs = BYTES_PER_QUERY * n / (ms / 1e3) / 1e9
 
-    line = {"metric": "closest-point queries/s (10M pts, 82k tris)" if args.config == "large" else
-            "closest-point queries/s", "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
+    line = {"metric": metric_name(args.config), "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": desc, "queries": n, "tris": mesh.n_tris, "l2": "flushed between steps (256 MB write)",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
-            "gpu_launches": 2 * args.steps,
+            "gpu_launches": 3 * args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
-                         "frac": achieved / alu_peak, "traffic": None, "kernel": "k_query_thread",
+                         "frac": achieved / alu_peak, "traffic": profiled_traffic(args.config, n),
+                         "kernel": "k_query_thread + k_query_warp (one query pass)",
                          "peak_kind": f"FP32 FMA lanes x max SM clock from {pk_kind} peaks",
                          "hbm_achieved_gbs": hbm_gbs, "hbm_peak_gbs": pk.get("hbm_gbs"),
                          "hbm_frac": hbm_gbs / float(pk.get("hbm_gbs", 6800.0))},
@@ -317,6 +353,35 @@ def main():
         fb_ms = e0.elapsed_time(e1) / fsteps
         line["fwd_bwd"] = {"value": dq.shape[0] / (fb_ms / 1e3), "unit": "queries/s", "ms_per_step": fb_ms,
                            "workload": WORKLOADS["diff"][0] + "; loss = sum d^2, grads to points and vertices"}
+        # batching: 256 meshes behind one persistent launch (graph) vs one launch per mesh
+        meshes, bq = W.workload_batch(256)
+        bidx = p2m.P2MIndex.batch([(m_.verts, m_.tris) for m_ in meshes])
+        boff = np.concatenate([[0], np.cumsum([len(x) for x in bq])]).astype(np.int64)
+        bpts = torch.from_numpy(np.concatenate(bq)).to(dev)
+        del bq
+        nb = bpts.shape[0]
+        bout = (torch.empty(nb, device=dev), torch.empty(nb, 3, device=dev),
+                torch.empty(nb, device=dev, dtype=torch.int32), torch.empty(nb, 3, device=dev))
+        res = {}
+        for label, mode, graph in (("batched", 0, True), ("per_mesh", 1, False)):
+            for _ in range(2):
+                bidx.batch_query(bpts, boff, mode=mode, use_graph=graph, out=bout)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            bsteps = max(3, min(args.steps, 10))
+            e0.record()
+            for _ in range(bsteps):
+                bidx.batch_query(bpts, boff, mode=mode, use_graph=graph, out=bout)
+            e1.record()
+            torch.cuda.synchronize()
+            res[label] = e0.elapsed_time(e1) / bsteps
+        line["batch"] = {"value": nb / (res["batched"] / 1e3), "unit": "queries/s", "ms_per_step": res["batched"],
+                         "per_mesh_value": nb / (res["per_mesh"] / 1e3), "per_mesh_ms": res["per_mesh"],
+                         "speedup": res["per_mesh"] / res["batched"], "queries": nb, "meshes": len(meshes),
+                         "tris": int(sum(m_.n_tris for m_ in meshes)),
+                         "workload": "256 noisy geodesic spheres / capped cylinders, T log-uniform [500, 200k], "
+                                     "Q log-uniform [1k, 1M]; one persistent launch in a CUDA graph vs one launch per mesh"}
+        del bidx, bpts, bout
     else:
         line["e2e"] = None
 

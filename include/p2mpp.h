@@ -72,8 +72,10 @@ typedef struct {
     float build_eps_rel;
     /* Nearest-site grid resolution per axis; 0 = automatic [0]. */
     int nn_grid_res;
-    /* Query schedule: 0 automatic, 1 thread per query, 2 warp per query, 3 site-binned
-     * thread per query with shared-memory staged lists [0]. */
+    /* Query schedule [0]: 0 = queries sorted by the Morton code of their grid cell, then
+     * thread per query for lists up to 64 entries and a warp-cooperative best-first scan
+     * for longer lists; 1 = thread per query for every list; 2 = warp per query for every
+     * list; 3 = as 0 without the sort.  All give identical results. */
     int schedule;
     /* Deterministic vertex-gradient accumulation (fixed-point integer atomics) [1]. */
     int deterministic;

@@ -132,30 +132,37 @@ def geodesic_sphere(freq: int, radius: float = 1.0) -> Mesh:
     """Each icosahedron face split into freq^2 triangles, projected to the sphere: T = 20*freq^2."""
     v0, f0 = _icosahedron()
     n = max(1, int(freq))
-    key_to_id: dict = {}
-    verts = []
-
-    def vid(a, b, c, i, j):
-        # point with integer barycentric weights (n-i-j, i, j) on face (a,b,c); shared edges
-        # and corners are keyed by the vertex ids carrying non-zero weight.
-        w = {a: n - i - j, b: i, c: j}
-        key = tuple(sorted((k, wt) for k, wt in w.items() if wt))
-        if key not in key_to_id:
-            p = sum(wt * v0[k] for k, wt in key) / n
-            key_to_id[key] = len(verts)
-            verts.append(p / np.linalg.norm(p))
-        return key_to_id[key]
-
+    ii, jj = np.meshgrid(np.arange(n + 1), np.arange(n + 1), indexing="ij")
+    keep = ii + jj <= n
+    ii, jj = ii[keep], jj[keep]
+    local = -np.ones((n + 1, n + 1), np.int64)
+    local[ii, jj] = np.arange(len(ii))
+    # triangles of one face in local grid ids
+    a_i, a_j = np.meshgrid(np.arange(n), np.arange(n), indexing="ij")
+    up = a_i + a_j <= n - 1
+    dn = a_i + a_j <= n - 2
+    t_up = np.stack([local[a_i[up], a_j[up]], local[a_i[up] + 1, a_j[up]], local[a_i[up], a_j[up] + 1]], 1)
+    t_dn = np.stack([local[a_i[dn] + 1, a_j[dn]], local[a_i[dn] + 1, a_j[dn] + 1], local[a_i[dn], a_j[dn] + 1]], 1)
+    tloc = np.concatenate([t_up, t_dn], 0)
+    npf = len(ii)
+    pts = []
     tris = []
-    for a, b, c in f0:
-        for i in range(n):
-            for j in range(n - i):
-                p0, p1, p2 = vid(a, b, c, i, j), vid(a, b, c, i + 1, j), vid(a, b, c, i, j + 1)
-                tris.append((p0, p1, p2))
-                if i + j < n - 1:
-                    p3 = vid(a, b, c, i + 1, j + 1)
-                    tris.append((p1, p3, p2))
-    return _mesh(np.array(verts) * radius, tris)
+    for k, (a, b, c) in enumerate(f0):
+        p = ((n - ii - jj)[:, None] * v0[a] + ii[:, None] * v0[b] + jj[:, None] * v0[c]) / n
+        pts.append(p)
+        tris.append(tloc + k * npf)
+    pts = np.concatenate(pts, 0)
+    tris = np.concatenate(tris, 0)
+    # points on shared edges / corners coincide exactly up to rounding: merge them
+    key = np.round(pts * 1e9).astype(np.int64)
+    _, first, inv = np.unique(key, axis=0, return_index=True, return_inverse=True)
+    inv = inv.reshape(-1)
+    order = np.argsort(first)
+    remap = np.empty_like(order)
+    remap[order] = np.arange(len(order))
+    verts = pts[first[order]]
+    verts /= np.linalg.norm(verts, axis=1, keepdims=True)
+    return _mesh(verts * radius, remap[inv][tris])
 
 
 def splitmix64(x: np.ndarray) -> np.ndarray:

@@ -29,12 +29,13 @@ __global__ void k_tri_precompute(const float* __restrict__ verts, const int32_t*
     const float3 n = make_float3(dop(e0.y, e1.z, e0.z, e1.y), dop(e0.z, e1.x, e0.x, e1.z), dop(e0.x, e1.y, e0.y, e1.x));
     const float nn = dot3(n, n);
     // Too thin to project onto (sin^2 of the angle at v0 below 1e-12): edges only.
-    const float inv_nn = (nn > 1e-12f * l0 * l1 && nn > 0.0f) ? 1.0f / nn : __int_as_float(0x7fc00000);
+    const bool flat = !(nn > 1e-12f * l0 * l1 && nn > 0.0f);
+    const float rn = flat ? 0.0f : rsqrtf(nn);
     float4* r = rec + 4 * (int64_t)f;
-    r[0] = make_float4(a.x, a.y, a.z, l0 > 0.0f ? 1.0f / l0 : 0.0f);
-    r[1] = make_float4(e0.x, e0.y, e0.z, l1 > 0.0f ? 1.0f / l1 : 0.0f);
-    r[2] = make_float4(e1.x, e1.y, e1.z, l2 > 0.0f ? 1.0f / l2 : 0.0f);
-    r[3] = make_float4(n.x, n.y, n.z, inv_nn);
+    r[0] = make_float4(n.x * rn, n.y * rn, n.z * rn, flat ? __int_as_float(0x7fc00000) : rn);
+    r[1] = make_float4(a.x, a.y, a.z, l0 > 0.0f ? 1.0f / l0 : 0.0f);
+    r[2] = make_float4(e0.x, e0.y, e0.z, l1 > 0.0f ? 1.0f / l1 : 0.0f);
+    r[3] = make_float4(e1.x, e1.y, e1.z, l2 > 0.0f ? 1.0f / l2 : 0.0f);
 
     // minimal enclosing sphere
     float3 cen;

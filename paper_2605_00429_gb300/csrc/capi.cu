@@ -211,8 +211,10 @@ static int build_mesh(MeshData& m, const p2m_build_params& prm, p2m_index* h, cu
     // host Voronoi, augmentation, corner balls, lists, nearest-site grid
     P2M_TRY(build_partition(m, prm, h, s));
     // list-scan schedule: 1 = thread per query for every list, 2 = warp per query for every
-    // list, 0/3 = thread per query for lists up to 64 entries and warp per query beyond
+    // list, 0/3 = thread per query for lists up to 64 entries and warp per query beyond;
+    // 0 also processes the queries in grid-cell Morton order
     m.long_row = prm.schedule == 1 ? 0x7fffffff : (prm.schedule == 2 ? 0 : 64);
+    m.sorted = prm.schedule == 0;
     st.ms_total = now_ms() - t0;
     return P2M_OK;
 }

@@ -25,13 +25,14 @@ __device__ __forceinline__ float dop(float a, float b, float c, float d) {
     return r + err;
 }
 
-// Triangle record, 4 x float4 = 64 bytes:
-//   r0 = (v0.xyz, 1/|e0|^2)     e0 = v1 - v0
-//   r1 = (e0.xyz, 1/|e1|^2)     e1 = v2 - v0
-//   r2 = (e1.xyz, 1/|e2|^2)     e2 = v2 - v1
-//   r3 = (n.xyz, 1/|n|^2)       n = e0 x e1 (compensated); 1/|n|^2 is NaN for a triangle
-//                               too thin to project onto (then only the edges are used)
-// A zero-length edge stores 1/|e|^2 = 0, which clamps its parameter to the start vertex.
+// Triangle record, 4 x float4 = 64 bytes; the first 32 bytes alone give a plane bound:
+//   r0 = (u.xyz, 1/|n|)         n = e0 x e1 (compensated), u = n/|n| the unit normal
+//   r1 = (v0.xyz, 1/|e0|^2)     e0 = v1 - v0
+//   r2 = (e0.xyz, 1/|e1|^2)     e1 = v2 - v0
+//   r3 = (e1.xyz, 1/|e2|^2)     e2 = v2 - v1
+// 1/|n| is NaN and u = 0 for a triangle too thin to project onto (then only the edges are
+// used, and the plane bound is 0).  A zero-length edge stores 1/|e|^2 = 0, which clamps its
+// parameter to the start vertex.
 struct TriRec {
     float4 r0, r1, r2, r3;
 };
@@ -46,43 +47,51 @@ __device__ __forceinline__ TriRec load_tri(const float4* __restrict__ tri, int f
     return t;
 }
 
+// Lower bound |u . (q - v0)| of the distance from q to triangle f (its supporting plane),
+// from the first half of the record.
+__device__ __forceinline__ float tri_plane_dist(const float4* __restrict__ tri, int f, float3 q) {
+    const float4* p = tri + 4 * (int64_t)f;
+    const float4 a = __ldg(p), b = __ldg(p + 1);
+    return fabsf(dot3(f3(a), q - f3(b)));
+}
+
 // Exact squared distance from q to the triangle; (s, t) locate the closest point
 // p = v0 + s e0 + t e1 (barycentrics (1 - s - t, s, t)).
 //
 // Interior test by triple products: the projection of q onto the plane has in-plane
-// coordinates s = ((w x e1) . n) / |n|^2 and t = ((e0 x w) . n) / |n|^2 with w = q - v0.
-// If they lie in the triangle, d^2 = (w . n)^2 / |n|^2.  Otherwise the closest point is on
-// an edge whose supporting line separates the projection from the triangle; every edge is
-// clamped and the best one kept.
+// coordinates s = ((w x e1) . u) / |n| and t = ((e0 x w) . u) / |n| with w = q - v0.
+// If they lie in the triangle, d^2 = (w . u)^2.  Otherwise the closest point is on an edge
+// whose supporting line separates the projection from the triangle; every edge is clamped
+// and the best one kept.
 __device__ __forceinline__ float tri_dist2(float3 q, const TriRec& T, float& s_out, float& t_out) {
-    const float3 v0 = f3(T.r0), e0 = f3(T.r1), e1 = f3(T.r2), n = f3(T.r3);
-    const float inv_nn = T.r3.w;
+    const float3 u = f3(T.r0), v0 = f3(T.r1), e0 = f3(T.r2), e1 = f3(T.r3);
+    const float inv_n = T.r0.w;
     const float3 w = q - v0;
-    const float s = dot3(cross3(w, e1), n) * inv_nn;
-    const float t = dot3(cross3(e0, w), n) * inv_nn;
+    const float s = dot3(cross3(w, e1), u) * inv_n;
+    const float t = dot3(cross3(e0, w), u) * inv_n;
     if (s >= 0.0f && t >= 0.0f && s + t <= 1.0f) {
-        const float h = dot3(w, n);
+        const float h = dot3(w, u);
         s_out = s;
         t_out = t;
-        return h * h * inv_nn;
+        return h * h;
     }
     // edge v0 -> v1 (t = 0)
-    float u = clamp01(dot3(w, e0) * T.r0.w);
-    float3 r = w - u * e0;
+    float k = clamp01(dot3(w, e0) * T.r1.w);
+    float3 r = w - k * e0;
     float best = dot3(r, r);
-    float bs = u, bt = 0.0f;
+    float bs = k, bt = 0.0f;
     // edge v0 -> v2 (s = 0)
-    u = clamp01(dot3(w, e1) * T.r1.w);
-    r = w - u * e1;
+    k = clamp01(dot3(w, e1) * T.r2.w);
+    r = w - k * e1;
     float d = dot3(r, r);
-    if (d < best) { best = d; bs = 0.0f; bt = u; }
+    if (d < best) { best = d; bs = 0.0f; bt = k; }
     // edge v1 -> v2 (s + t = 1)
     const float3 w1 = w - e0;
     const float3 e2 = e1 - e0;
-    u = clamp01(dot3(w1, e2) * T.r2.w);
-    r = w1 - u * e2;
+    k = clamp01(dot3(w1, e2) * T.r3.w);
+    r = w1 - k * e2;
     d = dot3(r, r);
-    if (d < best) { best = d; bs = 1.0f - u; bt = u; }
+    if (d < best) { best = d; bs = 1.0f - k; bt = k; }
     s_out = bs;
     t_out = bt;
     return best;
@@ -90,7 +99,7 @@ __device__ __forceinline__ float tri_dist2(float3 q, const TriRec& T, float& s_o
 
 // Closest point and barycentrics from a record and (s, t).
 __device__ __forceinline__ float3 tri_point(const TriRec& T, float s, float t) {
-    const float3 v0 = f3(T.r0), e0 = f3(T.r1), e1 = f3(T.r2);
+    const float3 v0 = f3(T.r1), e0 = f3(T.r2), e1 = f3(T.r3);
     return make_float3(fmaf(t, e1.x, fmaf(s, e0.x, v0.x)), fmaf(t, e1.y, fmaf(s, e0.y, v0.y)),
                        fmaf(t, e1.z, fmaf(s, e0.z, v0.z)));
 }

@@ -143,7 +143,7 @@ __global__ void k_chunk_boxes(const int64_t* __restrict__ row_off64, const int32
                 f = row_tri[j];
                 lo = f3(tlo[f]);
                 hi = f3(thi[f]);
-                nsum = f3(tri[4 * (int64_t)f + 3]);  // area-weighted normal (e0 x e1)
+                nsum = f3(tri[4 * (int64_t)f]);  // unit normal
             }
             for (int o = 16; o > 0; o >>= 1) {
                 lo.x = fminf(lo.x, __shfl_xor_sync(0xffffffffu, lo.x, o));
@@ -162,7 +162,7 @@ __global__ void k_chunk_boxes(const int64_t* __restrict__ row_off64, const int32
             float hmin = INFINITY, hmax = -INFINITY;
             if (f >= 0) {
                 const float4* r = tri + 4 * (int64_t)f;
-                const float3 v0 = f3(r[0]), e0 = f3(r[1]), e1 = f3(r[2]);
+                const float3 v0 = f3(r[1]), e0 = f3(r[2]), e1 = f3(r[3]);
                 const float a = dot3(n, v0), b = dot3(n, e0), c = dot3(n, e1);
                 hmin = fminf(a, fminf(a + b, a + c));
                 hmax = fmaxf(a, fmaxf(a + b, a + c));

@@ -119,6 +119,7 @@ struct MeshData {
     DevBuf d_sites, d_refs, d_row_off, d_row_tri, d_cell_off, d_cell_site, d_chunk_off, d_cbox, d_l1_off, d_l1box;
     int64_t nnz = 0, n_chunks = 0;
     int long_row = 64;
+    bool sorted = true;          // process queries in grid-cell Morton order
     int G = 0;
     float3 g_lo{}, g_hi{}, g_inv_h{};
     p2m_stats stats{};
