@@ -205,6 +205,50 @@ def run_reference(args, rank, world):
     print(json.dumps(line), flush=True)
 
 
+def run_ablation(args):
+    """Table 4 counterpart: each mesh built without and with site augmentation; list
+    statistics (Max / Avg / Queried), query rate and build time.  One JSON line per build."""
+    import torch
+    import paper_2605_00429_gb300 as p2m
+    from paper_2605_00429_gb300 import build as pbuild
+    pbuild.build()
+    torch.cuda.set_device(0)
+    cases = [
+        ("sphere: icosphere(5), 20,480 faces, no noise; 1M queries uniform in 1.2x bbox",
+         lambda: (W.icosphere(5), None)),
+        ("noisy sphere: icosphere(6) + noise, 81,920 faces; 1M queries as config 2",
+         lambda: W.workload_large(1_000_000)),
+        ("cylinder + cone 256x64, 51,968 faces; 1M queries as config 3",
+         lambda: W.workload_symmetric(1_000_000, n_ang=256, n_ax=64)),
+    ]
+    for desc, make in cases:
+        mesh, q = make()
+        if q is None:
+            q = W.queries_uniform_box(mesh, 1_000_000, 1.2, seed=1)
+        pts = torch.from_numpy(q).cuda()
+        for aux in (0, 1):
+            t0 = time.perf_counter()
+            idx = p2m.P2MIndex(mesh.verts, mesh.tris, enable_aux=aux)
+            build_ms = (time.perf_counter() - t0) * 1e3
+            st = idx.stats()
+            c = idx.counters(pts)
+            out = idx.query(pts)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            for _ in range(5):
+                idx.query(pts, out=out)
+            e1.record()
+            torch.cuda.synchronize()
+            ms = e0.elapsed_time(e1) / 5
+            print(json.dumps({"ablation": desc, "aux": aux, "build_ms": build_ms, "query_ms": ms,
+                              "queries_per_s": len(q) / (ms / 1e3), "max_list": st["max_row"],
+                              "avg_list": st["avg_row"], "queried_entries": c["row_entries"] / len(q),
+                              "queried_exact": c["exact_tests"] / len(q), "sites": st["n_sites"],
+                              "aux_sites": st["n_aux_sites"], "nnz": st["nnz"]}), flush=True)
+            del idx
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -216,7 +260,10 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip fwd+bwd and e2e legs")
     ap.add_argument("--schedule", type=int, default=0)
+    ap.add_argument("--ablation", action="store_true", help="Table-4 style runs with / without site augmentation")
     args = ap.parse_args()
+    if args.ablation:
+        return run_ablation(args)
     args.warmup = max(args.warmup, 3)
 
     rank, world, local = _env_int("RANK", 0), _env_int("WORLD_SIZE", 1), _env_int("LOCAL_RANK", 0)

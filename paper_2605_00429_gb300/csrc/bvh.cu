@@ -157,7 +157,7 @@ __global__ void k_karras(const unsigned* __restrict__ code, int n, int* __restri
 }
 
 // Bottom-up refit: each leaf walks up; the second child to arrive at a node finishes it.
-__global__ void k_refit(int n, const int* __restrict__ sorted_prim, const float4* __restrict__ plo,
+__global__ void k_refit(int n, int leaf_sorted, const int* __restrict__ sorted_prim, const float4* __restrict__ plo,
                         const float4* __restrict__ phi, const int* __restrict__ left, const int* __restrict__ right,
                         const int* __restrict__ parent_int, const int* __restrict__ parent_leaf,
                         unsigned* __restrict__ visits, float4* __restrict__ nlo, float4* __restrict__ nhi,
@@ -176,7 +176,9 @@ __global__ void k_refit(int n, const int* __restrict__ sorted_prim, const float4
                 const int p = sorted_prim[~c[h]];
                 blo[h] = plo[p];
                 bhi[h] = phi[p];
-                blo[h].w = __int_as_float(~p);  // leaf reference: ~original primitive id
+                // leaf reference: ~sorted position (primitives renumbered in leaf order) or
+                // ~original primitive id
+                blo[h].w = __int_as_float(leaf_sorted ? ~(~c[h]) : ~p);
             } else {
                 blo[h] = __ldcg(&nlo[c[h]]);
                 bhi[h] = __ldcg(&nhi[c[h]]);
@@ -193,11 +195,16 @@ __global__ void k_refit(int n, const int* __restrict__ sorted_prim, const float4
     }
 }
 
-int build_lbvh(const float4* d_lo, const float4* d_hi, int n, float3 c_lo, float3 c_hi, Bvh& out, cudaStream_t s) {
+int build_lbvh(const float4* d_lo, const float4* d_hi, int n, float3 c_lo, float3 c_hi, Bvh& out, cudaStream_t s,
+               DevBuf* order_out) {
     out.n_prims = n;
     if (n <= 0) return fail(P2M_ERR_INVALID_ARG, "BVH over zero primitives");
     if (n == 1) {
         out.root = ~0;
+        if (order_out) {
+            P2M_TRY(order_out->alloc(sizeof(int)));
+            P2M_CUDA_TRY(cudaMemsetAsync(order_out->p, 0, sizeof(int), s));
+        }
         return P2M_OK;
     }
     out.root = 0;
@@ -229,11 +236,34 @@ int build_lbvh(const float4* d_lo, const float4* d_hi, int n, float3 c_lo, float
                                                  pint.as<int>(), pleaf.as<int>());
     P2M_CUDA_TRY(cudaGetLastError());
     P2M_CUDA_TRY(cudaMemsetAsync(visits.p, 0, sizeof(unsigned) * n, s));
-    k_refit<<<(n + 255) / 256, 256, 0, s>>>(n, idx2.as<int>(), d_lo, d_hi, left.as<int>(), right.as<int>(),
+    k_refit<<<(n + 255) / 256, 256, 0, s>>>(n, order_out ? 1 : 0, idx2.as<int>(), d_lo, d_hi, left.as<int>(), right.as<int>(),
                                             pint.as<int>(), pleaf.as<int>(), visits.as<unsigned>(), nlo.as<float4>(),
                                             nhi.as<float4>(), out.nodes.as<BNode>());
     P2M_CUDA_TRY(cudaGetLastError());
     P2M_CUDA_TRY(cudaStreamSynchronize(s));  // temporaries are released on return
+    if (order_out) *order_out = std::move(idx2);
+    return P2M_OK;
+}
+
+// dst[k] = src[order[k]] for records of `per` float4 each.
+__global__ void k_gather_f4(const float4* __restrict__ src, float4* __restrict__ dst, const int* __restrict__ order,
+                            int n, int per) {
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < (int64_t)n * per;
+         t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = t / per, j = t % per;
+        dst[t] = src[(int64_t)order[k] * per + j];
+    }
+}
+
+int gather_f4(DevBuf& buf, const int* d_order, int n, int per, cudaStream_t s) {
+    DevBuf out;
+    P2M_TRY(out.alloc(sizeof(float4) * (size_t)n * per));
+    const int64_t tot = (int64_t)n * per;
+    k_gather_f4<<<(int)std::min<int64_t>((tot + 255) / 256, 152 * 64), 256, 0, s>>>(buf.as<float4>(), out.as<float4>(),
+                                                                                   d_order, n, per);
+    P2M_CUDA_TRY(cudaGetLastError());
+    P2M_CUDA_TRY(cudaStreamSynchronize(s));
+    buf = std::move(out);
     return P2M_OK;
 }
 
@@ -242,7 +272,8 @@ int build_lbvh(const float4* d_lo, const float4* d_hi, int n, float3 c_lo, float
 __global__ void k_bvh_closest(const BNode* __restrict__ nodes, int root, const float4* __restrict__ tri,
                               const float* __restrict__ pts, const int32_t* __restrict__ idx, const int* __restrict__ count,
                               int64_t n, float* __restrict__ dist, float* __restrict__ closest,
-                              int32_t* __restrict__ tri_out, float* __restrict__ bary, unsigned* status) {
+                              int32_t* __restrict__ tri_out, float* __restrict__ bary, unsigned* status,
+                              const int32_t* __restrict__ orig) {
     const int64_t nn = count ? (int64_t)*count : n;
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < nn; k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t i = idx ? idx[k] : k;
@@ -252,7 +283,7 @@ __global__ void k_bvh_closest(const BNode* __restrict__ nodes, int root, const f
     const int f = (int)(key & 0xffffffffu);
     const float d2 = __uint_as_float((unsigned)(key >> 32));
     dist[i] = sqrtf(d2);
-    if (tri_out) tri_out[i] = f;
+    if (tri_out) tri_out[i] = orig ? __ldg(orig + f) : f;
     if (closest) {
         const TriRec T = load_tri(tri, f);
         const float3 p = tri_point(T, s, t);
@@ -272,7 +303,8 @@ int launch_bvh_closest(const MeshView& m, const float* d_pts, const int32_t* d_i
     const int64_t want = (n + bs - 1) / bs;
     const int64_t blocks = d_count ? std::min<int64_t>(want, 152 * 8) : std::min<int64_t>(want, 152 * 64);
     k_bvh_closest<<<(unsigned)std::max<int64_t>(blocks, 1), bs, 0, s>>>(m.bvh, m.bvh_root, m.tri, d_pts, d_idx, d_count,
-                                                                         n, d_dist, d_closest, d_tri, d_bary, d_status);
+                                                                         n, d_dist, d_closest, d_tri, d_bary, d_status,
+                                                                         m.orig);
     P2M_CUDA_TRY(cudaGetLastError());
     return P2M_OK;
 }

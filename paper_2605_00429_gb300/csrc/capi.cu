@@ -2,6 +2,7 @@
 // dispatch.  The compute lives in the kernels of bvh.cu / lists.cu / grid.cu / query.cu and
 // the host Voronoi code of voronoi.cpp.
 #include <atomic>
+#include <cstdlib>
 #include <chrono>
 #include <thread>
 #include <cmath>
@@ -25,9 +26,30 @@ int fail(int code, const std::string& msg) {
     return code;
 }
 
+// Host-side fault injection for tests: P2M_FAULT=alloc:K makes the K-th device allocation
+// (counted from the last change of the variable) fail as out of memory.
+static bool inject_alloc_fault() {
+    static std::mutex mu;
+    static std::string last;
+    static long count = 0;
+    const char* e = std::getenv("P2M_FAULT");
+    std::lock_guard<std::mutex> lock(mu);
+    const std::string v = e ? e : "";
+    if (v != last) { last = v; count = 0; }
+    if (v.rfind("alloc:", 0) != 0) return false;
+    return ++count == std::atol(v.c_str() + 6);
+}
+
+bool inject_fault(const char* what) {
+    const char* e = std::getenv("P2M_FAULT");
+    return e && std::strcmp(e, what) == 0;
+}
+
 int DevBuf::alloc(size_t nbytes) {
     release();
     if (nbytes == 0) nbytes = 16;
+    if (inject_alloc_fault())
+        return fail(P2M_ERR_OOM, "cudaMalloc(" + std::to_string(nbytes) + "): injected allocation failure");
     cudaError_t e = cudaMalloc(&p, nbytes);
     if (e != cudaSuccess) {
         p = nullptr;
@@ -47,6 +69,7 @@ int DevBuf::ensure(size_t nbytes) {
 MeshView MeshData::view() const {
     MeshView v{};
     v.tri = d_tri.as<const float4>();
+    v.orig = d_orig.as<const int32_t>();
     v.tsph = d_tsph.as<const float4>();
     v.bvh = bvh.nodes.as<const BNode>();
     v.bvh_root = bvh.root;
@@ -204,7 +227,15 @@ static int build_mesh(MeshData& m, const p2m_build_params& prm, p2m_index* h, cu
         P2M_TRY(tri_boxes(m.d_verts.as<float>(), m.d_tris.as<int32_t>(), T, m.d_tlo.as<float4>(), m.d_thi.as<float4>(), s));
         const float3 clo = make_float3((float)m.bb_lo[0], (float)m.bb_lo[1], (float)m.bb_lo[2]);
         const float3 chi = make_float3((float)m.bb_hi[0], (float)m.bb_hi[1], (float)m.bb_hi[2]);
-        P2M_TRY(build_lbvh(m.d_tlo.as<float4>(), m.d_thi.as<float4>(), T, clo, chi, m.bvh, s));
+        P2M_TRY(build_lbvh(m.d_tlo.as<float4>(), m.d_thi.as<float4>(), T, clo, chi, m.bvh, s, &m.d_orig));
+        // renumber the triangle data in BVH leaf (Morton) order: list entries, which K1 emits
+        // in leaf order, then read mostly contiguous records
+        P2M_TRY(gather_f4(m.d_tri, m.d_orig.as<int>(), T, 4, s));
+        P2M_TRY(gather_f4(m.d_tsph, m.d_orig.as<int>(), T, 1, s));
+        P2M_TRY(gather_f4(m.d_tlo, m.d_orig.as<int>(), T, 1, s));
+        P2M_TRY(gather_f4(m.d_thi, m.d_orig.as<int>(), T, 1, s));
+        m.orig.resize(T);
+        P2M_CUDA_TRY(cudaMemcpy(m.orig.data(), m.d_orig.p, sizeof(int32_t) * T, cudaMemcpyDeviceToHost));
     }
     double t3 = now_ms();
     st.ms_lbvh = t3 - t2;
@@ -384,8 +415,10 @@ int p2m_get_lists(const p2m_index* h, int mesh, int64_t* h_offsets, int32_t* h_t
         P2M_CUDA_TRY(cudaMemcpy(off.data(), m->d_row_off.p, sizeof(int32_t) * (S + 1), cudaMemcpyDeviceToHost));
     if (h_offsets)
         for (int64_t i = 0; i <= S; ++i) h_offsets[i] = off[i];
-    if (h_tri_ids && m->nnz > 0)
+    if (h_tri_ids && m->nnz > 0) {
         P2M_CUDA_TRY(cudaMemcpy(h_tri_ids, m->d_row_tri.p, sizeof(int32_t) * m->nnz, cudaMemcpyDeviceToHost));
+        for (int64_t k = 0; k < m->nnz; ++k) h_tri_ids[k] = m->orig[h_tri_ids[k]];  // caller's triangle ids
+    }
     return P2M_OK;
 }
 

@@ -14,6 +14,7 @@ namespace p2m {
 // ----------------------------------------------------------------------------- errors
 
 void set_error(const std::string& msg);
+bool inject_fault(const char* what);  // P2M_FAULT == what (host-side test fault injection)
 int fail(int code, const std::string& msg);
 
 #define P2M_CUDA_TRY(expr)                                                              \
@@ -75,7 +76,8 @@ struct Bvh {
 
 // Everything the query path of one mesh reads, as raw device pointers (for kernels).
 struct MeshView {
-    const float4* tri;      // [T][4] triangle records (see geom.cuh)
+    const float4* tri;      // [T][4] triangle records (see geom.cuh), in BVH leaf order
+    const int32_t* orig;    // [T] original triangle id of each leaf-order position
     const float4* tsph;     // [T] bounding spheres (c.xyz, r)
     const BNode* bvh;       // triangle BVH
     int bvh_root;
@@ -114,7 +116,8 @@ struct MeshData {
     std::vector<double> ball_c;       // [B*3]
     std::vector<double> ball_r;       // [B]
     // device
-    DevBuf d_verts, d_tris, d_tri, d_tsph, d_tlo, d_thi;
+    DevBuf d_verts, d_tris, d_tri, d_tsph, d_tlo, d_thi, d_orig;
+    std::vector<int32_t> orig;   // host copy of d_orig
     Bvh bvh;
     DevBuf d_sites, d_refs, d_row_off, d_row_tri, d_cell_off, d_cell_site, d_chunk_off, d_cbox, d_l1_off, d_l1box;
     int64_t nnz = 0, n_chunks = 0;
@@ -132,8 +135,11 @@ struct MeshData {
 int launch_tri_precompute(const float* d_verts, const int32_t* d_tris, int n_tris, float4* d_tri,
                           float4* d_tsph, cudaStream_t s);
 // K0: LBVH over primitive boxes (lo[i], hi[i]); scene centroid bounds given.
+// With order_out, primitives are renumbered in leaf (Morton) order: leaves reference sorted
+// positions and order_out[k] receives the original id of position k.
 int build_lbvh(const float4* d_lo, const float4* d_hi, int n, float3 c_lo, float3 c_hi, Bvh& out,
-               cudaStream_t s);
+               cudaStream_t s, DevBuf* order_out = nullptr);
+int gather_f4(DevBuf& buf, const int* d_order, int n, int per, cudaStream_t s);  // buf[k] = buf[order[k]]
 int tri_boxes(const float* d_verts, const int32_t* d_tris, int n_tris, float4* lo, float4* hi,
               cudaStream_t s);
 // K5: exact closest triangle by BVH branch and bound.  Queries are d_pts[d_idx[k]] for

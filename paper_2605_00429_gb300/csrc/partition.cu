@@ -246,7 +246,14 @@ int build_partition(MeshData& m, const p2m_build_params& prm, p2m_index* h, cuda
     int64_t n_dense = 0;
     if (prm.enable_aux) {
         n_aux = augment(ss, m, prm, n_dense);
-        if (n_aux > 0 && ss.triangulate_from(n_vsites, (uint64_t)prm.seed + 1, err)) return fail(P2M_ERR_INTERNAL, err);
+        if (n_aux > 0) {
+            // triangulate all sites again in one Morton order: inserting the auxiliary sites
+            // into the finished triangulation would open very large cavities around the
+            // degenerate interior tetrahedra they are meant to break up
+            ss.dt.init(ss.lat.R);
+            ss.vid.clear();
+            if (ss.triangulate_from(0, (uint64_t)prm.seed + 1, err)) return fail(P2M_ERR_INTERNAL, err);
+        }
     }
     double t2 = ms_now();
     st.ms_aug = t2 - t1;

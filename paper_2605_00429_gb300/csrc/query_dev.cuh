@@ -131,7 +131,7 @@ __device__ __forceinline__ void write_result(const MeshView& m, int64_t i, unsig
                                              int32_t* __restrict__ tri_out, float* __restrict__ bary) {
     const int f = (int)(key & 0xffffffffu);
     dist[i] = sqrtf(__uint_as_float((unsigned)(key >> 32)));
-    if (tri_out) tri_out[i] = f;
+    if (tri_out) tri_out[i] = __ldg(m.orig + f);
     if (closest) {
         const TriRec T = load_tri(m.tri, f);
         const float3 p = tri_point(T, s, t);

@@ -7,6 +7,7 @@
 #include <thread>
 
 #include "host_geom.h"
+#include "p2m_internal.h"
 #include "voronoi.h"
 
 namespace p2m {
@@ -45,7 +46,7 @@ int SiteSet::triangulate_from(int first, uint64_t seed, std::string& err) {
         const int i = o.second;
         int tries = 0;
         while (true) {
-            const int r = dt.insert(pts[i], rng);
+            const int r = inject_fault("delaunay") ? INSERT_BROKEN : dt.insert(pts[i], rng);
             if (r >= 0) { vid[i] = r; break; }
             if (r == INSERT_BROKEN) { err = "Delaunay insertion broke the triangulation"; return -1; }
             if (++tries > 64) { err = "could not place a site after 64 jitters"; return -1; }
