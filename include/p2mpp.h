@@ -60,7 +60,8 @@ typedef struct {
     /* tau = tau_scale x mean edge length [2.0] (Section 3.2 "Choice of Parameters"). */
     float tau_scale;
     /* A tau-cell is dense when its Voronoi-vertex count exceeds density_factor x the median
-     * count of non-empty tau-cells [8.0] and density_min [32]. */
+     * count of non-empty tau-cells [8.0] and density_min [256].  (Symmetric meshes put
+     * thousands of Voronoi vertices in one tau-cell; noise-perturbed ones about a hundred.) */
     float density_factor;
     int density_min;
     /* Auxiliary sites per ring: 12 (icosahedron directions) or 6 (octahedron) [12]. */
@@ -100,6 +101,8 @@ typedef struct {
     double bbox_diag;
     /* stage wall times in milliseconds */
     double ms_upload, ms_tri, ms_lbvh, ms_delaunay, ms_cells, ms_aug, ms_proj, ms_k1, ms_grid, ms_total;
+    /* Voronoi vertices per non-empty tau-cell of the augmentation: median and maximum */
+    int64_t aug_cell_median, aug_cell_max;
 } p2m_stats;
 
 /* Per-call query counters (Section 4.1, Table 1 "Queried"). */

@@ -40,7 +40,8 @@ class Stats(ctypes.Structure):
         [(n, ctypes.c_int64) for n in ("grid_res", "grid_entries", "grid_max", "n_delaunay_tets", "n_dense_cells")] + \
         [("domain_lo", ctypes.c_double * 3), ("domain_hi", ctypes.c_double * 3), ("bbox_diag", ctypes.c_double)] + \
         [(n, ctypes.c_double) for n in ("ms_upload", "ms_tri", "ms_lbvh", "ms_delaunay", "ms_cells", "ms_aug",
-                                        "ms_proj", "ms_k1", "ms_grid", "ms_total")]
+                                        "ms_proj", "ms_k1", "ms_grid", "ms_total")] + \
+        [("aug_cell_median", ctypes.c_int64), ("aug_cell_max", ctypes.c_int64)]
 
     def as_dict(self):
         d = {}

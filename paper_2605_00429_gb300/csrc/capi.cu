@@ -263,7 +263,7 @@ int p2m_default_params(p2m_build_params* out) {
     out->enable_aux = 1;
     out->tau_scale = 2.0f;
     out->density_factor = 8.0f;
-    out->density_min = 32;
+    out->density_min = 256;
     out->ring_sites = 12;
     out->ring_radius_scale = 1.299038f;  // 0.75 * sqrt(3)
     out->build_eps_rel = 1e-6f;

@@ -23,13 +23,15 @@ void Clipper::box(const double lo[3], const double hi[3]) {
     F = {{0, 2, 6, 4}, {1, 5, 7, 3}, {0, 4, 5, 1}, {2, 3, 7, 6}, {0, 1, 3, 2}, {4, 6, 7, 5}};
 }
 
-double Clipper::radius_from(const double p[3]) const {
+double Clipper::radius_from(const double p[3]) const { return std::sqrt(radius2_from(p)); }
+
+double Clipper::radius2_from(const double p[3]) const {
     double r2 = 0;
     for (int i = 0; i < n_verts(); ++i) {
         const double dx = V[3 * i] - p[0], dy = V[3 * i + 1] - p[1], dz = V[3 * i + 2] - p[2];
         r2 = std::max(r2, dx * dx + dy * dy + dz * dz);
     }
-    return std::sqrt(r2);
+    return r2;
 }
 
 bool Clipper::clip(const double n[3], double d, double tol) {

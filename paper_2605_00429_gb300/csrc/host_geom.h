@@ -57,6 +57,7 @@ struct Clipper {
     // keep the half-space n . x <= d; returns false if the polytope became empty
     bool clip(const double n[3], double d, double tol);
     double radius_from(const double p[3]) const;  // max distance from p to a corner
+    double radius2_from(const double p[3]) const;  // its square
     int n_verts() const { return (int)(V.size() / 3); }
 
 private:

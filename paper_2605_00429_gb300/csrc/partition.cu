@@ -116,7 +116,7 @@ struct PointHash {
 // site plus a ring of auxiliary sites on an enclosing sphere for each; ring sites that fall
 // near an existing site or inside another flagged cell's bounding sphere are dropped.
 // Returns the number of auxiliary sites appended to ss.pts.
-static int augment(SiteSet& ss, const MeshData& m, const p2m_build_params& prm, int64_t& n_dense) {
+static int augment(SiteSet& ss, MeshData& m, const p2m_build_params& prm, int64_t& n_dense) {
     n_dense = 0;
     // tau from the mean edge length
     double sum = 0;
@@ -154,6 +154,8 @@ static int augment(SiteSet& ss, const MeshData& m, const p2m_build_params& prm, 
     for (auto& kv : count) vals.push_back(kv.second);
     std::nth_element(vals.begin(), vals.begin() + vals.size() / 2, vals.end());
     const double median = vals[vals.size() / 2];
+    m.stats.aug_cell_median = (int64_t)median;
+    m.stats.aug_cell_max = *std::max_element(vals.begin(), vals.end());
     const double thresh = std::max((double)prm.density_min, prm.density_factor * median);
     std::vector<std::array<double, 3>> centres;
     for (auto& kv : count) {
@@ -198,6 +200,10 @@ static int augment(SiteSet& ss, const MeshData& m, const p2m_build_params& prm, 
         }
     return added;
 }
+
+// At most this many balls per site (4 per lane of the K1 warp); only cells that reach a
+// degenerate region (fan centres, symmetry axes) have more corners than this.
+constexpr int kMaxBalls = 128;
 
 int build_partition(MeshData& m, const p2m_build_params& prm, p2m_index* h, cudaStream_t s) {
     p2m_stats& st = m.stats;
@@ -365,11 +371,58 @@ int build_partition(MeshData& m, const p2m_build_params& prm, p2m_index* h, cuda
                         if (d + ur[a] < ur[b] || (d + ur[a] == ur[b] && b < a)) keep[a] = 0;
                     }
                 }
+                std::vector<int> kept;
                 for (int a = 0; a < nb; ++a)
-                    if (keep[a]) {
+                    if (keep[a]) kept.push_back(a);
+                if ((int)kept.size() <= kMaxBalls) {
+                    for (int a : kept) {
                         m.ball_c.insert(m.ball_c.end(), &uc[3 * a], &uc[3 * a] + 3);
                         m.ball_r.push_back(ur[a]);
                     }
+                } else {
+                    // Too many corners (cells reaching a degenerate region have hundreds):
+                    // merge them into kMaxBalls enclosing balls.  Centres are picked by
+                    // farthest-point sampling; each corner joins its nearest centre c and
+                    // B(u, r) lies inside B(c, |u - c| + r), so the union only grows and the
+                    // list stays complete (any convex superset of the cell is valid for Eq. 3).
+                    const int k = (int)kept.size();
+                    std::vector<int> centre;
+                    std::vector<double> dmin(k, 1e300);
+                    int pick = 0;
+                    for (int a = 1; a < k; ++a)
+                        if (ur[kept[a]] > ur[kept[pick]]) pick = a;
+                    for (int c = 0; c < kMaxBalls; ++c) {
+                        centre.push_back(pick);
+                        const double* pc = &uc[3 * kept[pick]];
+                        int far = 0;
+                        for (int a = 0; a < k; ++a) {
+                            const double* pa = &uc[3 * kept[a]];
+                            const double d = std::sqrt((pa[0] - pc[0]) * (pa[0] - pc[0]) + (pa[1] - pc[1]) * (pa[1] - pc[1]) +
+                                                       (pa[2] - pc[2]) * (pa[2] - pc[2]));
+                            dmin[a] = std::min(dmin[a], d);
+                            if (dmin[a] > dmin[far]) far = a;
+                        }
+                        pick = far;
+                    }
+                    std::vector<double> R(kMaxBalls, 0.0);
+                    for (int a = 0; a < k; ++a) {
+                        const double* pa = &uc[3 * kept[a]];
+                        int best = 0;
+                        double bd = 1e300;
+                        for (int c = 0; c < kMaxBalls; ++c) {
+                            const double* pc = &uc[3 * kept[centre[c]]];
+                            const double d = std::sqrt((pa[0] - pc[0]) * (pa[0] - pc[0]) + (pa[1] - pc[1]) * (pa[1] - pc[1]) +
+                                                       (pa[2] - pc[2]) * (pa[2] - pc[2]));
+                            if (d < bd) { bd = d; best = c; }
+                        }
+                        R[best] = std::max(R[best], bd + ur[kept[a]]);
+                    }
+                    for (int c = 0; c < kMaxBalls; ++c) {
+                        const double* pc = &uc[3 * kept[centre[c]]];
+                        m.ball_c.insert(m.ball_c.end(), pc, pc + 3);
+                        m.ball_r.push_back(R[c]);
+                    }
+                }
             } else {
                 double p[3];
                 for (int k = 0; k < 3; ++k) p[k] = m.site_pos[3 * i + k];

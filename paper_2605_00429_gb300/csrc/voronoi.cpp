@@ -89,6 +89,7 @@ void SiteSet::neighbour_csr() {
 // Corners of every site's cell: D cut by the bisectors of its Delaunay neighbours,
 // nearest neighbour first.  Threads split the sites.
 int SiteSet::clip_cells(const double dom_lo[3], const double dom_hi[3], double diag, int n_threads) {
+    constexpr int kMaxClip = 256;
     const int n = (int)pts.size();
     cell_off.assign(n + 1, 0);
     std::vector<std::vector<double>> corners(n);
@@ -112,7 +113,14 @@ int SiteSet::clip_cells(const double dom_lo[3], const double dom_hi[3], double d
                 order.push_back({d2, nb_id[k]});
             }
             std::sort(order.begin(), order.end());
+            int used = 0;
             for (auto& o : order) {
+                // Nearest first: a neighbour t can cut the cell only if its bisector, at
+                // distance |s - t| / 2 from s, comes within the cell's radius about s.  After
+                // kMaxClip neighbours the clip stops; the cell is then a superset of the true
+                // one, which is still a valid region for Eq. 3.
+                if (0.25 * o.first > C.radius2_from(ps) * (1.0 + 1e-9) + tol * tol) break;
+                if (++used > kMaxClip) break;
                 double pt[3];
                 world(o.second, pt);
                 double nrm[3] = {pt[0] - ps[0], pt[1] - ps[1], pt[2] - ps[2]};
