@@ -74,14 +74,17 @@ typedef struct {
     /* Nearest-site grid resolution per axis; 0 = automatic [0]. */
     int nn_grid_res;
     /* Query schedule [0]: 0 = queries sorted by the Morton code of their grid cell, then
-     * thread per query for lists up to 64 entries and a warp-cooperative best-first scan
-     * for longer lists; 1 = thread per query for every list; 2 = warp per query for every
-     * list; 3 = as 0 without the sort.  All give identical results. */
+     * thread per query for lists up to long_list entries and a warp-cooperative best-first
+     * scan for longer lists; 1 = thread per query for every list; 2 = warp per query for
+     * every list; 3 = as 0 without the sort.  All give identical results. */
     int schedule;
     /* Deterministic vertex-gradient accumulation (fixed-point integer atomics) [1]. */
     int deterministic;
     /* Seed of the site jitter used to break exact Delaunay degeneracies [1]. */
     int seed;
+    /* Lists longer than this take the warp-cooperative scan in schedules 0 and 3; 0 picks
+     * the default (256) [0]. */
+    int long_list;
 } p2m_build_params;
 
 /* Build statistics (Section 4.1, Table 1: Max / Avg list length) and stage timings. */

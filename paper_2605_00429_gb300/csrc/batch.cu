@@ -183,7 +183,7 @@ int run_batch_query(p2m_index* h, const float* d_pts, const int64_t* h_off, floa
     if (!b.tuned) {
         // autotuner: time each (tile, long_row) candidate on this batch, keep the fastest
         const int tiles[] = {1024, 4096};
-        const int longs[] = {0, 64, 256};
+        const int longs[] = {0, 64, 256, 1024};
         cudaEvent_t e0, e1;
         P2M_CUDA_TRY(cudaEventCreate(&e0));
         P2M_CUDA_TRY(cudaEventCreate(&e1));

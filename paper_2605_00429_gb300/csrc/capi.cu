@@ -83,7 +83,7 @@ MeshView MeshData::view() const {
     v.l1box = d_l1box.as<const float4>();
     v.long_row = long_row;
     v.cell_off = d_cell_off.as<const int32_t>();
-    v.cell_site = d_cell_site.as<const int32_t>();
+    v.cell_site = d_cell_site.as<const float4>();
     v.G = G;
     v.lo = g_lo;
     v.hi = g_hi;
@@ -140,6 +140,7 @@ static int validate_params(const p2m_build_params& p) {
     if (!(p.build_eps_rel >= 0.0f && p.build_eps_rel < 1e-2f)) return fail(P2M_ERR_INVALID_ARG, "build_eps_rel out of range");
     if (p.nn_grid_res < 0 || p.nn_grid_res > 1024) return fail(P2M_ERR_INVALID_ARG, "nn_grid_res out of range");
     if (p.schedule < 0 || p.schedule > 3) return fail(P2M_ERR_INVALID_ARG, "schedule must be 0..3");
+    if (p.long_list < 0) return fail(P2M_ERR_INVALID_ARG, "long_list must be >= 0");
     return P2M_OK;
 }
 
@@ -242,9 +243,10 @@ static int build_mesh(MeshData& m, const p2m_build_params& prm, p2m_index* h, cu
     // host Voronoi, augmentation, corner balls, lists, nearest-site grid
     P2M_TRY(build_partition(m, prm, h, s));
     // list-scan schedule: 1 = thread per query for every list, 2 = warp per query for every
-    // list, 0/3 = thread per query for lists up to 64 entries and warp per query beyond;
+    // list, 0/3 = thread per query for lists up to long_list entries and warp per query beyond;
     // 0 also processes the queries in grid-cell Morton order
-    m.long_row = prm.schedule == 1 ? 0x7fffffff : (prm.schedule == 2 ? 0 : 64);
+    const int long_list = prm.long_list > 0 ? prm.long_list : 256;
+    m.long_row = prm.schedule == 1 ? 0x7fffffff : (prm.schedule == 2 ? 0 : long_list);
     m.sorted = prm.schedule == 0;
     st.ms_total = now_ms() - t0;
     return P2M_OK;

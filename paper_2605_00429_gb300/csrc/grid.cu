@@ -6,7 +6,7 @@
 // Candidates of a grid cell with centre c and half-diagonal h: with d_nn(c) the nearest-
 // site distance, site s can win at a point x of the cell only if ||c - s|| <= d_nn(c) + 2h
 // (the triangle inequality twice).  Those sites come from a range query on a BVH of the
-// sites; each is then dropped if the whole cell is strictly closer to one of the 8 sites
+// sites; each is then dropped if the whole cell is strictly closer to one of the 16 sites
 // nearest to c (a linear test over the cell's corners, with a margin so that rounding
 // never drops a true candidate).
 #include <cub/device/device_scan.cuh>
@@ -16,7 +16,7 @@
 
 namespace p2m {
 
-constexpr int kKnn = 8;
+constexpr int kKnn = 16;
 constexpr int kGridStack = 64;
 
 struct GridParams {
@@ -88,7 +88,7 @@ __device__ __forceinline__ bool box_closer_to(float3 lo, float3 hi, float3 s, fl
 
 template <bool FILL>
 __global__ void k_grid(GridParams g, const BNode* __restrict__ nodes, int root, const float4* __restrict__ sites,
-                       int n_sites, int64_t* __restrict__ count, const int64_t* __restrict__ off, int32_t* __restrict__ out,
+                       int n_sites, int64_t* __restrict__ count, const int64_t* __restrict__ off, float4* __restrict__ out,
                        unsigned* status) {
     const int64_t n_cells = (int64_t)g.G * g.G * g.G;
     for (int64_t cid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; cid < n_cells;
@@ -120,7 +120,8 @@ __global__ void k_grid(GridParams g, const BNode* __restrict__ nodes, int root, 
                 if (t < 0 || t == s) continue;
                 if (box_closer_to(lo, hi, ps, f3(__ldg(sites + t)), g.margin)) return;
             }
-            if (FILL) out[base + k] = s;
+            // candidate stored with its coordinates (id in w) so a query reads one contiguous run
+            if (FILL) out[base + k] = make_float4(ps.x, ps.y, ps.z, __int_as_float(s));
             ++k;
         };
         if (root < 0) {
@@ -181,10 +182,10 @@ int build_grid(MeshData& m, const Bvh& site_bvh, int G, unsigned* status, cudaSt
     P2M_CUDA_TRY(cudaMemcpyAsync(&total, off.as<int64_t>() + n_cells, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     P2M_CUDA_TRY(cudaStreamSynchronize(s));
     if (total > 0x7fffffffLL) return fail(P2M_ERR_LIMIT, "nearest-site grid too large");
-    P2M_TRY(m.d_cell_site.alloc(sizeof(int32_t) * std::max<int64_t>(total, 1)));
+    P2M_TRY(m.d_cell_site.alloc(sizeof(float4) * std::max<int64_t>(total, 1)));
     P2M_TRY(m.d_cell_off.alloc(sizeof(int32_t) * (n_cells + 1)));
     k_grid<true><<<blocks, 128, 0, s>>>(g, nodes, site_bvh.root, m.d_sites.as<float4>(), n_sites, nullptr,
-                                        off.as<int64_t>(), m.d_cell_site.as<int32_t>(), status);
+                                        off.as<int64_t>(), m.d_cell_site.as<float4>(), status);
     P2M_CUDA_TRY(cudaGetLastError());
     k_i64_to_i32<<<256, 256, 0, s>>>(off.as<int64_t>(), m.d_cell_off.as<int32_t>(), n_cells + 1);
     P2M_CUDA_TRY(cudaGetLastError());

@@ -20,7 +20,7 @@ struct BatchState {
     DevBuf longq, rest;  // queues of the warp pass and of the BVH pass
     int n_tiles = 0;
     int tile = 0;        // queries per tile picked by the autotuner
-    int long_row = 64;   // lists longer than this take the warp-per-query pass
+    int long_row = 256;  // lists longer than this take the warp-per-query pass
     bool tuned = false;
     float tune_ms = 0.f;
     int grid_thread = 0, grid_warp = 0, grid_bvh = 0;

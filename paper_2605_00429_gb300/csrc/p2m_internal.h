@@ -90,7 +90,7 @@ struct MeshView {
     const int32_t* l1_off;  // [S+1] first level-1 box (32 chunks = 1024 entries) of each list
     const float4* l1box;    // [n_l1][2]
     const int32_t* cell_off;// [G^3+1] nearest-site grid CSR
-    const int32_t* cell_site;
+    const float4* cell_site;// candidates: (x, y, z, site id as int bits)
     int G;                  // grid cells per axis (0 => no grid: every query takes the BVH path)
     float3 lo;              // domain D lower corner
     float3 inv_h;           // 1 / grid cell size
@@ -121,7 +121,7 @@ struct MeshData {
     Bvh bvh;
     DevBuf d_sites, d_refs, d_row_off, d_row_tri, d_cell_off, d_cell_site, d_chunk_off, d_cbox, d_l1_off, d_l1box;
     int64_t nnz = 0, n_chunks = 0;
-    int long_row = 64;
+    int long_row = 256;
     bool sorted = true;          // process queries in grid-cell Morton order
     int G = 0;
     float3 g_lo{}, g_hi{}, g_inv_h{};

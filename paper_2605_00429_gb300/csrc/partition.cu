@@ -482,7 +482,7 @@ int build_partition(MeshData& m, const p2m_build_params& prm, p2m_index* h, cuda
             const double spacing = std::sqrt(std::max(area, 1e-300) / std::max(1, n_vsites));
             double ext = 0;
             for (int k = 0; k < 3; ++k) ext = std::max(ext, m.dom_hi[k] - m.dom_lo[k]);
-            G = (int)std::lround(ext / (1.5 * spacing));
+            G = (int)std::lround(ext / (1.1 * spacing));
             G = std::max(8, std::min(G, 192));
         }
         std::vector<float4> lo(S), hi(S);

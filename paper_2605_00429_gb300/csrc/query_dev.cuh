@@ -27,8 +27,8 @@ __device__ __forceinline__ int nearest_site(const MeshView& m, float3 q, int cel
     float bd = INFINITY, sd = INFINITY;
     int bs = -1;
     for (int j = j0; j < j1; ++j) {
-        const int s = __ldg(m.cell_site + j);
-        const float4 p = __ldg(m.sites + s);
+        const float4 p = __ldg(m.cell_site + j);
+        const int s = __float_as_int(p.w);
         const float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
         const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         if (d2 < bd || (d2 == bd && s < bs)) {
@@ -47,8 +47,8 @@ __device__ __forceinline__ int nearest_site(const MeshView& m, float3 q, int cel
         double best = 1e300;
         int bi = -1;
         for (int j = j0; j < j1; ++j) {
-            const int s = __ldg(m.cell_site + j);
-            const float4 p = __ldg(m.sites + s);
+            const float4 p = __ldg(m.cell_site + j);
+            const int s = __float_as_int(p.w);
             const float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
             if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) > lim) continue;
             const double ex = (double)q.x - (double)p.x, ey = (double)q.y - (double)p.y, ez = (double)q.z - (double)p.z;
