@@ -77,6 +77,7 @@ MeshView MeshData::view() const {
     v.refs = d_refs.as<const float4>();
     v.row_off = d_row_off.as<const int32_t>();
     v.row_tri = d_row_tri.as<const int32_t>();
+    v.row_key = d_row_key.as<const float>();
     v.chunk_off = d_chunk_off.as<const int32_t>();
     v.cbox = d_cbox.as<const float4>();
     v.l1_off = d_l1_off.as<const int32_t>();
@@ -240,14 +241,15 @@ static int build_mesh(MeshData& m, const p2m_build_params& prm, p2m_index* h, cu
     }
     double t3 = now_ms();
     st.ms_lbvh = t3 - t2;
-    // host Voronoi, augmentation, corner balls, lists, nearest-site grid
-    P2M_TRY(build_partition(m, prm, h, s));
     // list-scan schedule: 1 = thread per query for every list, 2 = warp per query for every
     // list, 0/3 = thread per query for lists up to long_list entries and warp per query beyond;
-    // 0 also processes the queries in grid-cell Morton order
+    // 0 also processes the queries in grid-cell Morton order.  Known before the lists are
+    // built: the lists scanned per thread are stored ordered by their lower bound.
     const int long_list = prm.long_list > 0 ? prm.long_list : 256;
     m.long_row = prm.schedule == 1 ? 0x7fffffff : (prm.schedule == 2 ? 0 : long_list);
     m.sorted = prm.schedule == 0;
+    // host Voronoi, augmentation, corner balls, lists, nearest-site grid
+    P2M_TRY(build_partition(m, prm, h, s));
     st.ms_total = now_ms() - t0;
     return P2M_OK;
 }

@@ -14,6 +14,7 @@
 #include <cmath>
 
 #include <cub/device/device_scan.cuh>
+#include <cub/device/device_segmented_sort.cuh>
 
 #include "geom.cuh"
 #include "host.h"
@@ -218,6 +219,54 @@ __global__ void k_parent_boxes(const int32_t* __restrict__ child_off, const int3
     }
 }
 
+// Key of every list entry: ||ref_s - c_f|| - r_f - (rounding radius of ref_s), a lower bound
+// of the distance from the site's reference point to triangle f; q - ref gives, by the
+// triangle inequality, key - ||q - ref|| <= ||q - c_f|| - r_f <= d(q, f).
+__global__ void k_entry_keys(const int64_t* __restrict__ row_off64, int n_sites, const int32_t* __restrict__ row_tri,
+                             const float4* __restrict__ refs, const float4* __restrict__ tsph, float* __restrict__ key) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int s = warp; s < n_sites; s += nwarps) {
+        const float4 r = refs[s];
+        for (int64_t j = row_off64[s] + lane; j < row_off64[s + 1]; j += 32) {
+            const float4 c = tsph[row_tri[j]];
+            const float dx = r.x - c.x, dy = r.y - c.y, dz = r.z - c.z;
+            const float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+            // rounded down so that FP32 error never raises a lower bound
+            key[j] = (d - c.w - r.w) * (1.0f - 1e-6f) - 1e-30f;
+        }
+    }
+}
+
+// Segment ends for the segmented sort: lists longer than long_row stay in BVH order (an
+// empty segment), shorter ones are sorted by key.
+__global__ void k_sort_segments(const int64_t* __restrict__ row_off64, int n_sites, int long_row,
+                                int* __restrict__ beg, int* __restrict__ end) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s < n_sites; s += gridDim.x * blockDim.x) {
+        const int64_t b = row_off64[s], e = row_off64[s + 1];
+        beg[s] = (int)b;
+        end[s] = (e - b <= long_row) ? (int)e : (int)b;
+    }
+}
+
+// Copies the entries of the long (unsorted) lists from (ki, ti) to (ko, to).
+__global__ void k_copy_long(const int64_t* __restrict__ row_off64, int n_sites, int long_row,
+                            const float* __restrict__ ki, const int32_t* __restrict__ ti, float* __restrict__ ko,
+                            int32_t* __restrict__ to) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int s = warp; s < n_sites; s += nwarps) {
+        const int64_t b = row_off64[s], e = row_off64[s + 1];
+        if (e - b <= long_row) continue;
+        for (int64_t j = b + lane; j < e; j += 32) {
+            ko[j] = ki[j];
+            to[j] = ti[j];
+        }
+    }
+}
+
 __global__ void k_i64_to_i32(const int64_t* __restrict__ a, int32_t* __restrict__ b, int64_t n) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
         b[i] = (int32_t)a[i];
@@ -253,6 +302,38 @@ int build_lists(MeshData& m, const float4* d_balls, const int64_t* d_ball_off, i
     P2M_CUDA_TRY(cudaGetLastError());
     k_i64_to_i32<<<64, 256, 0, s>>>(off64.as<int64_t>(), m.d_row_off.as<int32_t>(), n_sites + 1);
     P2M_CUDA_TRY(cudaGetLastError());
+    // entry keys; lists scanned per thread are sorted by key (nearest first)
+    {
+        const int kb = std::max(1, std::min((n_sites + 7) / 8, 152 * 16));
+        P2M_TRY(m.d_row_key.alloc(sizeof(float) * std::max<int64_t>(nnz, 1)));
+        k_entry_keys<<<kb, 256, 0, s>>>(off64.as<int64_t>(), n_sites, m.d_row_tri.as<int32_t>(), m.d_refs.as<float4>(),
+                                        m.d_tsph.as<float4>(), m.d_row_key.as<float>());
+        P2M_CUDA_TRY(cudaGetLastError());
+        if (nnz > 0) {
+            DevBuf beg, end, key2, tri2, tmp3;
+            P2M_TRY(beg.alloc(sizeof(int) * n_sites));
+            P2M_TRY(end.alloc(sizeof(int) * n_sites));
+            P2M_TRY(key2.alloc(sizeof(float) * nnz));
+            P2M_TRY(tri2.alloc(sizeof(int32_t) * nnz));
+            k_sort_segments<<<std::max(1, std::min((n_sites + 255) / 256, 4096)), 256, 0, s>>>(
+                off64.as<int64_t>(), n_sites, m.long_row, beg.as<int>(), end.as<int>());
+            P2M_CUDA_TRY(cudaGetLastError());
+            size_t tb3 = 0;
+            P2M_CUDA_TRY(cub::DeviceSegmentedSort::StableSortPairs(
+                nullptr, tb3, m.d_row_key.as<float>(), key2.as<float>(), m.d_row_tri.as<int32_t>(), tri2.as<int32_t>(),
+                (int)nnz, n_sites, beg.as<int>(), end.as<int>(), s));
+            P2M_TRY(tmp3.alloc(tb3 + 16));
+            P2M_CUDA_TRY(cub::DeviceSegmentedSort::StableSortPairs(
+                tmp3.p, tb3, m.d_row_key.as<float>(), key2.as<float>(), m.d_row_tri.as<int32_t>(), tri2.as<int32_t>(),
+                (int)nnz, n_sites, beg.as<int>(), end.as<int>(), s));
+            k_copy_long<<<kb, 256, 0, s>>>(off64.as<int64_t>(), n_sites, m.long_row, m.d_row_key.as<float>(),
+                                           m.d_row_tri.as<int32_t>(), key2.as<float>(), tri2.as<int32_t>());
+            P2M_CUDA_TRY(cudaGetLastError());
+            P2M_CUDA_TRY(cudaStreamSynchronize(s));
+            m.d_row_key = std::move(key2);
+            m.d_row_tri = std::move(tri2);
+        }
+    }
     // chunk boxes
     {
         DevBuf nch;

@@ -91,14 +91,26 @@ __device__ __forceinline__ unsigned long long scan_list(const MeshView& m, float
                                                         unsigned long long* counters) {
     const int r0 = __ldg(m.row_off + site), r1 = __ldg(m.row_off + site + 1);
     const int c0 = __ldg(m.chunk_off + site), c1 = __ldg(m.chunk_off + site + 1);
-    float bound = ref_bound(m, q, site);
+    const float4 ref = __ldg(m.refs + site);
+    const float rx = q.x - ref.x, ry = q.y - ref.y, rz = q.z - ref.z;
+    const float dq = sqrtf(fmaf(rx, rx, fmaf(ry, ry, rz * rz)));
+    float bound = fmaf(dq + ref.w, 1.0f + 9.6e-7f, m.prune_abs);
+    // a list of at most long_row entries is sorted by key = ||ref - c_f|| - r_f: once
+    // key - ||q - ref|| exceeds the bound, so does every later entry's lower bound
+    const bool sorted_list = r1 - r0 <= m.long_row;
+    const float dq_up = fmaf(dq, 1.0f + 9.6e-7f, m.prune_abs);
     unsigned long long best = ~0ull;
     int n_exact = 0, n_entries = 0;
-    for (int c = c0; c < c1; ++c) {
+    bool done = false;
+    for (int c = c0; c < c1 && !done; ++c) {
         if (!chunk_may_hit(m, c, q, bound)) continue;
         const int j0 = r0 + (c - c0) * kChunk, j1 = min(j0 + kChunk, r1);
-        if (COUNT) n_entries += j1 - j0;
         for (int j = j0; j < j1; ++j) {
+            if (sorted_list && __ldg(m.row_key + j) > bound + dq_up) {
+                done = true;
+                break;
+            }
+            if (COUNT) ++n_entries;
             const int f = __ldg(m.row_tri + j);
             const float4 sp = __ldg(m.tsph + f);
             const float dx = q.x - sp.x, dy = q.y - sp.y, dz = q.z - sp.z;
