@@ -10,6 +10,8 @@
 #include <algorithm>
 #include <cstring>
 
+#include <cub/device/device_radix_sort.cuh>
+
 #include "bvh_dev.cuh"
 #include "host.h"
 #include "query_dev.cuh"
@@ -29,6 +31,7 @@ struct BatchArgs {
     int4* longq;        // (query, site, mesh, 0)
     int2* rest;         // (query, mesh)
     int* ctr;           // [0] tile head, [1] long count, [2] rest count, [3] long head
+    const int32_t* perm;  // sorted position -> query (NULL: unsorted)
 };
 
 __global__ void __launch_bounds__(256) k_batch_thread(BatchArgs a) {
@@ -41,7 +44,8 @@ __global__ void __launch_bounds__(256) k_batch_thread(BatchArgs a) {
         if (t >= a.n_tiles) break;
         const int4 tile = __ldg(a.tiles + t);
         const MeshView& m = a.views[tile.x];
-        for (int64_t i = (int64_t)tile.y + threadIdx.x; i < tile.z; i += blockDim.x) {
+        for (int64_t k = (int64_t)tile.y + threadIdx.x; k < tile.z; k += blockDim.x) {
+            const int64_t i = a.perm ? (int64_t)__ldg(a.perm + k) : k;
             const float3 q = make_float3(a.pts[3 * i], a.pts[3 * i + 1], a.pts[3 * i + 2]);
             int cell;
             int site = -1;
@@ -97,6 +101,36 @@ __global__ void __launch_bounds__(128) k_batch_bvh(BatchArgs a, unsigned* status
     }
 }
 
+// Sort key of a query of a batch: (mesh << 24) | Morton code of its cell in that mesh's grid,
+// so that sorting keeps every mesh's queries in its own offset range (the tiles stay valid)
+// and makes neighbouring threads read the same lists.
+__device__ __forceinline__ unsigned spread8b(unsigned v) {
+    v &= 0xffu;
+    v = (v | (v << 8)) & 0x0300F00Fu;
+    v = (v | (v << 4)) & 0x030C30C3u;
+    v = (v | (v << 2)) & 0x09249249u;
+    return v;
+}
+
+__global__ void k_batch_keys(BatchArgs a, unsigned long long* __restrict__ key, int32_t* __restrict__ idx) {
+    for (int t = blockIdx.x; t < a.n_tiles; t += gridDim.x) {
+        const int4 tile = __ldg(a.tiles + t);
+        const MeshView& m = a.views[tile.x];
+        for (int64_t i = (int64_t)tile.y + threadIdx.x; i < tile.z; i += blockDim.x) {
+            const float3 q = make_float3(a.pts[3 * i], a.pts[3 * i + 1], a.pts[3 * i + 2]);
+            unsigned mc = 0xffffffu;
+            if (m.G > 0) {
+                const float fx = (q.x - m.lo.x) * m.inv_h.x, fy = (q.y - m.lo.y) * m.inv_h.y,
+                            fz = (q.z - m.lo.z) * m.inv_h.z;
+                if (fx >= 0.0f && fy >= 0.0f && fz >= 0.0f && fx < (float)m.G && fy < (float)m.G && fz < (float)m.G)
+                    mc = (spread8b((unsigned)fx) << 2) | (spread8b((unsigned)fy) << 1) | spread8b((unsigned)fz);
+            }
+            key[i] = ((unsigned long long)tile.x << 24) | mc;
+            idx[i] = (int32_t)i;
+        }
+    }
+}
+
 static int persistent_blocks(const void* kernel, int threads) {
     int per_sm = 1, dev = 0, sms = 152;
     cudaGetDevice(&dev);
@@ -106,8 +140,22 @@ static int persistent_blocks(const void* kernel, int threads) {
 }
 
 // The launch sequence of one batched query (captured into the graph when requested).
-static int launch_batch(BatchState& b, const BatchArgs& a, unsigned* status, cudaStream_t s) {
+static int launch_batch(BatchState& b, const BatchArgs& a0, unsigned* status, cudaStream_t s) {
+    BatchArgs a = a0;
     P2M_CUDA_TRY(cudaMemsetAsync(a.ctr, 0, 4 * sizeof(int), s));
+    if (b.sort_tmp_bytes) {
+        // Morton sort of every mesh's queries inside its own range
+        const int64_t N = b.offsets.back();
+        unsigned long long* k0 = b.sort_keys.as<unsigned long long>();
+        int32_t* i0 = b.sort_idx.as<int32_t>();
+        k_batch_keys<<<std::max(1, std::min(a.n_tiles, 152 * 32)), 256, 0, s>>>(a, k0, i0);
+        P2M_CUDA_TRY(cudaGetLastError());
+        cub::DoubleBuffer<unsigned long long> dk(k0, k0 + N);
+        cub::DoubleBuffer<int32_t> dv(i0, i0 + N);
+        size_t tb = b.sort_tmp_bytes;
+        P2M_CUDA_TRY(cub::DeviceRadixSort::SortPairs(b.sort_tmp.p, tb, dk, dv, (int)N, 0, b.sort_end_bit, s));
+        a.perm = dv.Current();
+    }
     k_batch_thread<<<b.grid_thread, 256, 0, s>>>(a);
     k_batch_warp<<<b.grid_warp, 256, 0, s>>>(a);
     k_batch_bvh<<<b.grid_bvh, 128, 0, s>>>(a, status);
@@ -168,6 +216,17 @@ int run_batch_query(p2m_index* h, const float* d_pts, const int64_t* h_off, floa
         P2M_TRY(b.rest.ensure(sizeof(int2) * N));
         b.offsets = off;
         b.tuned = false;
+        // scratch of the per-mesh Morton sort (double buffers + radix-sort temporaries)
+        int mesh_bits = 1;
+        while ((1 << mesh_bits) < nm) ++mesh_bits;
+        b.sort_end_bit = 24 + mesh_bits;
+        P2M_TRY(b.sort_keys.ensure(sizeof(unsigned long long) * 2 * N));
+        P2M_TRY(b.sort_idx.ensure(sizeof(int32_t) * 2 * N));
+        size_t tb = 0;
+        P2M_CUDA_TRY(cub::DeviceRadixSort::SortPairs(nullptr, tb, (unsigned long long*)nullptr, (unsigned long long*)nullptr,
+                                                     (int32_t*)nullptr, (int32_t*)nullptr, (int)N, 0, b.sort_end_bit, s));
+        P2M_TRY(b.sort_tmp.ensure(tb + 16));
+        b.sort_tmp_bytes = tb;
     }
     BatchArgs a;
     a.views = b.views.as<const MeshView>();
@@ -179,6 +238,7 @@ int run_batch_query(p2m_index* h, const float* d_pts, const int64_t* h_off, floa
     a.longq = b.longq.as<int4>();
     a.rest = b.rest.as<int2>();
     a.ctr = b.counter.as<int>();
+    a.perm = nullptr;
     unsigned* status = index_status(h);
     if (!b.tuned) {
         // autotuner: time each (tile, long_row) candidate on this batch, keep the fastest

@@ -18,6 +18,9 @@ struct BatchState {
     DevBuf tiles;        // int4 work list: (mesh, q_begin, q_end, 0)
     DevBuf counter;      // tile head, long count, rest count, long head
     DevBuf longq, rest;  // queues of the warp pass and of the BVH pass
+    DevBuf sort_keys, sort_idx, sort_tmp;  // per-mesh Morton sort of the queries
+    size_t sort_tmp_bytes = 0;
+    int sort_end_bit = 24;
     int n_tiles = 0;
     int tile = 0;        // queries per tile picked by the autotuner
     int long_row = 256;  // lists longer than this take the warp-per-query pass
