@@ -48,10 +48,11 @@ struct p2m_index {
     p2m::DevBuf scratch_idx;   // compacted list of queries left to the BVH search
     p2m::BatchState batch;     // batched-query state (tile queue, graph)
     int device = 0;
-    // host-buffer query pipeline: two streams, each with its own device buffers
-    cudaStream_t streams[2] = {nullptr, nullptr};
-    p2m::DevBuf pipe[2][5];    // pts, dist, closest, tri, bary
-    p2m::DevBuf pipe_rest[2];
+    // host-buffer query pipeline: kPipe streams, each with its own device buffers
+    static constexpr int kPipe = 3;
+    cudaStream_t streams[kPipe] = {nullptr, nullptr, nullptr};
+    p2m::DevBuf pipe[kPipe][5];    // pts, dist, closest, tri, bary
+    p2m::DevBuf pipe_rest[kPipe];
     p2m::DevBuf grad_acc;      // fixed-point vertex-gradient accumulator
     ~p2m_index();
 };

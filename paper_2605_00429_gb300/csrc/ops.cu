@@ -106,6 +106,7 @@ int p2m_query_host(p2m_index* h, const float* h_pts, int64_t n, float* h_dist, f
     if (!h_pts || !h_dist) return fail(P2M_ERR_INVALID_ARG, "h_pts and h_dist must be non-NULL");
     MeshData& m = *h->meshes[0];
     cudaStream_t user = (cudaStream_t)stream;
+    constexpr int kSlots = p2m_index::kPipe;
     for (auto& st : h->streams)
         if (!st) P2M_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
     // the pipeline starts after the caller's earlier work on `stream`
@@ -114,8 +115,10 @@ int p2m_query_host(p2m_index* h, const float* h_pts, int64_t n, float* h_dist, f
     P2M_CUDA_TRY(cudaEventRecord(ev, user));
     for (auto& st : h->streams) P2M_CUDA_TRY(cudaStreamWaitEvent(st, ev, 0));
     cudaEventDestroy(ev);
-    const int64_t chunk = std::min<int64_t>(n, (int64_t)1 << 21);
-    for (int k = 0; k < 2; ++k) {
+    // Chunks of ~n/8 (at least 1M points) on kSlots streams: while one chunk computes, the
+    // copy engines move the previous chunk's results out and the next chunk's points in.
+    const int64_t chunk = std::min<int64_t>(n, std::max<int64_t>((int64_t)1 << 20, (n + 7) / 8));
+    for (int k = 0; k < kSlots; ++k) {
         P2M_TRY(h->pipe[k][0].ensure(sizeof(float) * 3 * chunk));
         P2M_TRY(h->pipe[k][1].ensure(sizeof(float) * chunk));
         if (h_closest) P2M_TRY(h->pipe[k][2].ensure(sizeof(float) * 3 * chunk));
@@ -123,7 +126,7 @@ int p2m_query_host(p2m_index* h, const float* h_pts, int64_t n, float* h_dist, f
         if (h_bary) P2M_TRY(h->pipe[k][4].ensure(sizeof(float) * 3 * chunk));
     }
     int slot = 0;
-    for (int64_t b = 0; b < n; b += chunk, slot ^= 1) {
+    for (int64_t b = 0; b < n; b += chunk, slot = (slot + 1) % kSlots) {
         const int64_t c = std::min(chunk, n - b);
         cudaStream_t s = h->streams[slot];
         DevBuf* P = h->pipe[slot];
