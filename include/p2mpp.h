@@ -159,8 +159,9 @@ int p2m_query(p2m_index* h, const float* d_pts, int64_t n, float* d_dist, float*
               int32_t* d_tri, float* d_bary, void* stream);
 
 /* The same query from host memory: copies h_pts in chunks to the device, runs the query
- * and copies the results back, overlapping copies and kernels on two streams.  Host
- * buffers may be pageable, but pinned (cudaHostAlloc) buffers are much faster.  Output
+ * and copies the results back.  Host
+ * buffers may be pageable, but pinned (cudaHostAlloc) buffers are much faster: chunks of
+ * about n/8 points on three streams overlap the copies with the kernels.  Output
  * pointers other than h_dist may be NULL.  Synchronous: returns when the outputs are in
  * host memory.  Errors: INVALID_ARG, OOM, CUDA. */
 int p2m_query_host(p2m_index* h, const float* h_pts, int64_t n, float* h_dist, float* h_closest,
