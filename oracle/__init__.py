@@ -11,6 +11,8 @@ Contents (each a plain, slow definition; see ``oracle.c`` for the C part):
 * ``nearest_site``  brute-force FP64 nearest site (cell locate, Section 3.3).
 * ``ball_margin``   per triangle, min over balls of d(u, f) - r_u (Eq. 3, Eq. 8).
 * ``aux_radius``    Eq. 8 for an off-surface site.
+* ``winding``       generalized winding number (inside / outside of a closed mesh), the
+                    plain definition behind the sign of the signed distance.
 * ``grad_analytic`` gradient of sum_i g_i d(q_i, M) w.r.t. queries and vertices, from the
                     closest-point barycentrics.
 * ``grad_fd``       central finite differences of the same loss, FP64.
@@ -57,6 +59,7 @@ def _load():
         _lib.orc_point_triangle.restype = ctypes.c_double
         _lib.orc_num_threads.restype = ctypes.c_int
         _lib.orc_dist_f64.argtypes = [P, I, P, I, P, I, P]
+        _lib.orc_winding.argtypes = [P, I, P, I, P, I, P]
     return _lib
 
 
@@ -113,6 +116,25 @@ def ball_margin(verts, tris, centres, radii):
     m = np.empty(t.shape[0])
     _load().orc_ball_margin(_ptr(v), v.shape[0], _ptr(t), t.shape[0], _ptr(c), _ptr(r), c.shape[0], _ptr(m))
     return m
+
+
+def winding(verts, tris, pts):
+    """Generalized winding number (sum of signed solid angles / 4 pi): 1 inside a closed
+    outward-oriented mesh, 0 outside."""
+    v = np.ascontiguousarray(verts, dtype=np.float32)
+    t = np.ascontiguousarray(tris, dtype=np.int32)
+    p = np.ascontiguousarray(pts, dtype=np.float32).reshape(-1, 3)
+    w = np.empty(p.shape[0])
+    _load().orc_winding(_ptr(v), v.shape[0], _ptr(t), t.shape[0], _ptr(p), p.shape[0], _ptr(w))
+    return w
+
+
+def signed_distance(verts, tris, pts, res=None):
+    """Signed distance of a closed mesh: -d(q, M) inside (winding number > 1/2), +d outside."""
+    if res is None:
+        res = closest(verts, tris, pts)
+    w = winding(verts, tris, pts)
+    return np.where(w > 0.5, -res["dist"], res["dist"]), w
 
 
 def aux_radius(site, corners, proj):

@@ -202,3 +202,27 @@ void orc_dist_f64(const double *verts, int64_t n_verts, const int32_t *tris, int
         dist[i] = sqrt(best);
     }
 }
+
+/* Generalized winding number of a closed, outward-oriented triangle mesh at each point:
+ * w(q) = sum_f Omega_f(q) / (4 pi), with Omega_f the signed solid angle of triangle f seen
+ * from q (van Oosterom & Strackee 1983: tan(Omega/2) = a.(b x c) / (|a||b||c| + (a.b)|c| +
+ * (a.c)|b| + (b.c)|a|), a, b, c the vertices relative to q).  w = 1 inside, 0 outside; it
+ * is the plain definition of inside/outside that the sign of the signed distance follows. */
+void orc_winding(const float *verts, int64_t n_verts, const int32_t *tris, int64_t n_tris, const float *pts,
+                 int64_t n, double *w) {
+    (void)n_verts;
+#pragma omp parallel for schedule(dynamic, 64)
+    for (int64_t i = 0; i < n; ++i) {
+        v3 q = mk(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]);
+        double sum = 0.0;
+        for (int64_t f = 0; f < n_tris; ++f) {
+            v3 a = sub(vert(verts, tris[3 * f]), q), b = sub(vert(verts, tris[3 * f + 1]), q),
+               c = sub(vert(verts, tris[3 * f + 2]), q);
+            double la = sqrt(dot(a, a)), lb = sqrt(dot(b, b)), lc = sqrt(dot(c, c));
+            double num = dot(a, crs(b, c));
+            double den = la * lb * lc + dot(a, b) * lc + dot(a, c) * lb + dot(b, c) * la;
+            sum += 2.0 * atan2(num, den);
+        }
+        w[i] = sum / (4.0 * 3.14159265358979323846);
+    }
+}

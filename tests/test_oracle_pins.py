@@ -217,3 +217,35 @@ def test_gradient_analytic_vs_fd():
     vi = rng.choice(m.n_verts, 12, replace=False)
     _, fv = oracle.grad_fd(m.verts, m.tris, q, g2, h, query_idx=[], vert_idx=vi)
     assert np.max(np.abs(fv - gv2[vi])) < 1e-5
+
+
+def test_winding_number_closed_forms():
+    """Winding number: 1 inside and 0 outside a closed outward-oriented mesh; on the cube the
+    answer is max|q_i| < 1/2, on the icosphere |q| below the inscribed radius / above 1."""
+    cube = W.unit_cube()
+    rng = np.random.default_rng(9)
+    q = (rng.random((3000, 3)) * 1.4 - 0.7).astype(np.float32)
+    a = np.abs(q.astype(np.float64)).max(1)
+    keep = np.abs(a - 0.5) > 1e-3
+    w = oracle.winding(cube.verts, cube.tris, q[keep])
+    assert np.allclose(w, (a[keep] < 0.5).astype(float), atol=1e-9)
+    ico = W.icosphere(3)
+    r = np.linalg.norm(q.astype(np.float64), axis=1) / 0.7 * 1.5
+    q2 = (q.astype(np.float64) / np.linalg.norm(q, axis=1, keepdims=True) * r[:, None]).astype(np.float32)
+    rr = np.linalg.norm(q2.astype(np.float64), axis=1)
+    keep = (rr < 0.98) | (rr > 1.0001)
+    w = oracle.winding(ico.verts, ico.tris, q2[keep])
+    assert np.allclose(w, (rr[keep] < 0.98).astype(float), atol=1e-9)
+    # reversing the orientation negates it
+    w_rev = oracle.winding(ico.verts, ico.tris[:, ::-1].copy(), q2[keep][:50])
+    assert np.allclose(w_rev, -w[:50], atol=1e-9)
+
+
+def test_signed_distance_sphere():
+    m = W.icosphere(4)
+    rng = np.random.default_rng(10)
+    q = (rng.normal(size=(2000, 3)) * 0.7).astype(np.float32)
+    sd, w = oracle.signed_distance(m.verts, m.tris, q)
+    r = np.linalg.norm(q.astype(np.float64), axis=1)
+    far = np.abs(r - 1.0) > 0.01
+    assert np.all(np.sign(sd[far]) == np.sign(r[far] - 1.0))
