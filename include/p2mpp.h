@@ -158,6 +158,16 @@ void p2m_destroy(p2m_index* h);
 int p2m_query(p2m_index* h, const float* d_pts, int64_t n, float* d_dist, float* d_closest,
               int32_t* d_tri, float* d_bary, void* stream);
 
+/* Signed distance (an extension: the paper computes unsigned distances): the
+ * query of p2m_query, then the sign of (q - p) . n with n the angle-weighted pseudonormal of
+ * the feature (face, edge or vertex) holding the closest point p: negative inside, positive
+ * outside a closed, outward-oriented mesh (meaningless for an open or inconsistently
+ * oriented one).  d_sdist[n] receives the signed distance; d_closest, d_tri, d_bary as in
+ * p2m_query (may be NULL; the index then uses its own scratch for d_tri / d_bary).
+ * Asynchronous.  Errors: INVALID_ARG, OOM, CUDA. */
+int p2m_query_signed(p2m_index* h, const float* d_pts, int64_t n, float* d_sdist, float* d_closest,
+                     int32_t* d_tri, float* d_bary, void* stream);
+
 /* The same query from host memory: copies h_pts in chunks to the device, runs the query
  * and copies the results back.  Host
  * buffers may be pageable, but pinned (cudaHostAlloc) buffers are much faster: chunks of

@@ -84,6 +84,7 @@ SIGNATURES = {
     "p2m_get_balls": ([_P, _I, _P, _P, _P], _I),
     "p2m_voronoi_cells": ([_P, _I64, _P, _P, _I, _P, _P, _P, _P], _I),
     "p2m_query_noalloc": ([_P, _P, _I64, _P, _P, _P, _P, _P], _I),
+    "p2m_query_signed": ([_P, _P, _I64, _P, _P, _P, _P, _P], _I),
 }
 NOALLOC_MAX_QUERIES = 262144
 
@@ -202,6 +203,20 @@ class P2MIndex:
         _check(lib().p2m_query(self._h, _dptr(pts), n, _dptr(dist), _dptr(closest), _dptr(tri), _dptr(bary),
                                _stream_ptr(stream)))
         return dist, closest, tri, bary
+
+    def query_signed(self, pts, stream=None):
+        """Signed distance (negative inside a closed outward-oriented mesh): returns
+        (sdist, closest, tri, bary) CUDA tensors."""
+        import torch
+        pts = pts.contiguous()
+        n = pts.shape[0]
+        sd = torch.empty(n, device=pts.device, dtype=torch.float32)
+        cl = torch.empty(n, 3, device=pts.device, dtype=torch.float32)
+        tr = torch.empty(n, device=pts.device, dtype=torch.int32)
+        ba = torch.empty(n, 3, device=pts.device, dtype=torch.float32)
+        _check(lib().p2m_query_signed(self._h, _dptr(pts), n, _dptr(sd), _dptr(cl), _dptr(tr), _dptr(ba),
+                                      _stream_ptr(stream)))
+        return sd, cl, tr, ba
 
     def query_host(self, pts: np.ndarray, h_dist=None, h_closest=None, h_tri=None, h_bary=None):
         """Host-memory query (copies inside the library).  Arrays may be pinned torch CPU

@@ -1,7 +1,9 @@
 // C ABI of libp2mpp.so: argument checking, index lifecycle, build orchestration and query
 // dispatch.  The compute lives in the kernels of bvh.cu / lists.cu / grid.cu / query.cu and
 // the host Voronoi code of voronoi.cpp.
+#include <array>
 #include <atomic>
+#include <unordered_map>
 #include <cstdlib>
 #include <chrono>
 #include <thread>
@@ -189,6 +191,61 @@ static int load_mesh(const float* verts, int64_t n_verts, const int32_t* tris, i
 
 // ----------------------------------------------------------------------------- build
 
+// Angle-weighted pseudonormals (FP64, uploaded as float4): the unit face normal, the edge
+// normal n_f1 + n_f2 of each edge's two faces (a boundary edge keeps its one face's normal),
+// and at every vertex the sum of its faces' normals weighted by their angles there.  The
+// sign of (q - p) . n at the feature (face, edge, vertex) holding the closest point p tells
+// inside from outside on a closed, outward-oriented mesh.
+static int build_pseudonormals(MeshData& m) {
+    const int64_t T = m.n_tris, V = m.n_verts;
+    std::vector<double> fn(3 * T, 0.0), vn(3 * V, 0.0);
+    auto vtx = [&](int64_t i, int k) { return (double)m.verts[3 * i + k]; };
+    for (int64_t f = 0; f < T; ++f) {
+        const int32_t* t = &m.tris[3 * f];
+        double e[3][3];
+        for (int j = 0; j < 3; ++j)
+            for (int k = 0; k < 3; ++k) e[j][k] = vtx(t[(j + 1) % 3], k) - vtx(t[j], k);  // edge j: v_j -> v_j+1
+        double n[3] = {e[0][1] * (-e[2][2]) - e[0][2] * (-e[2][1]), e[0][2] * (-e[2][0]) - e[0][0] * (-e[2][2]),
+                       e[0][0] * (-e[2][1]) - e[0][1] * (-e[2][0])};  // (v1 - v0) x (v2 - v0)
+        const double len = std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
+        if (!(len > 0)) continue;
+        for (int k = 0; k < 3; ++k) fn[3 * f + k] = n[k] / len;
+        for (int j = 0; j < 3; ++j) {
+            // angle at vertex j between edge j (outgoing) and the reversed edge j-1
+            const double* a = e[j];
+            const double* b = e[(j + 2) % 3];
+            const double la = std::sqrt(a[0] * a[0] + a[1] * a[1] + a[2] * a[2]);
+            const double lb = std::sqrt(b[0] * b[0] + b[1] * b[1] + b[2] * b[2]);
+            if (!(la > 0 && lb > 0)) continue;
+            const double c = std::max(-1.0, std::min(1.0, -(a[0] * b[0] + a[1] * b[1] + a[2] * b[2]) / (la * lb)));
+            const double ang = std::acos(c);
+            for (int k = 0; k < 3; ++k) vn[3 * (int64_t)t[j] + k] += ang * fn[3 * f + k];
+        }
+    }
+    std::unordered_map<uint64_t, std::array<double, 3>> en;
+    auto ekey = [](int a, int b) { return a < b ? ((uint64_t)a << 32 | (uint32_t)b) : ((uint64_t)b << 32 | (uint32_t)a); };
+    for (int64_t f = 0; f < T; ++f)
+        for (int j = 0; j < 3; ++j) {
+            auto& acc = en[ekey(m.tris[3 * f + j], m.tris[3 * f + (j + 1) % 3])];
+            for (int k = 0; k < 3; ++k) acc[k] += fn[3 * f + k];
+        }
+    auto unit4 = [](const double* v, float4& out) {
+        const double l = std::sqrt(v[0] * v[0] + v[1] * v[1] + v[2] * v[2]);
+        out = l > 0 ? make_float4((float)(v[0] / l), (float)(v[1] / l), (float)(v[2] / l), 0.f) : make_float4(0.f, 0.f, 0.f, 0.f);
+    };
+    std::vector<float4> srec(4 * T), vrec(V);
+    for (int64_t f = 0; f < T; ++f) {
+        unit4(&fn[3 * f], srec[4 * f]);
+        for (int j = 0; j < 3; ++j) unit4(en[ekey(m.tris[3 * f + j], m.tris[3 * f + (j + 1) % 3])].data(), srec[4 * f + 1 + j]);
+    }
+    for (int64_t v = 0; v < V; ++v) unit4(&vn[3 * v], vrec[v]);
+    P2M_TRY(m.d_snorm.alloc(sizeof(float4) * 4 * T));
+    P2M_TRY(m.d_vnorm.alloc(sizeof(float4) * V));
+    P2M_CUDA_TRY(cudaMemcpy(m.d_snorm.p, srec.data(), sizeof(float4) * 4 * T, cudaMemcpyHostToDevice));
+    P2M_CUDA_TRY(cudaMemcpy(m.d_vnorm.p, vrec.data(), sizeof(float4) * V, cudaMemcpyHostToDevice));
+    return P2M_OK;
+}
+
 static int build_mesh(MeshData& m, const p2m_build_params& prm, p2m_index* h, cudaStream_t s) {
     p2m_stats& st = m.stats;
     std::memset(&st, 0, sizeof(st));
@@ -208,6 +265,7 @@ static int build_mesh(MeshData& m, const p2m_build_params& prm, p2m_index* h, cu
     }
     // upload + K0b
     const int T = (int)m.n_tris;
+    P2M_TRY(build_pseudonormals(m));
     P2M_TRY(m.d_verts.alloc(sizeof(float) * 3 * m.n_verts));
     P2M_TRY(m.d_tris.alloc(sizeof(int32_t) * 3 * m.n_tris));
     P2M_CUDA_TRY(cudaMemcpyAsync(m.d_verts.p, m.verts.data(), sizeof(float) * 3 * m.n_verts, cudaMemcpyHostToDevice, s));

@@ -54,6 +54,7 @@ struct p2m_index {
     p2m::DevBuf pipe[kPipe][5];    // pts, dist, closest, tri, bary
     p2m::DevBuf pipe_rest[kPipe];
     p2m::DevBuf grad_acc;      // fixed-point vertex-gradient accumulator
+    p2m::DevBuf sign_scratch;  // triangle ids / barycentrics for the signed query
     ~p2m_index();
 };
 

@@ -61,9 +61,68 @@ __global__ void k_fixed_to_float_add(const unsigned long long* __restrict__ acc,
         out[i] += (float)((double)(long long)acc[i] * (1.0 / 4294967296.0));
 }
 
+// Sign of the distance from the closest feature's pseudonormal.  The feature comes from the
+// barycentrics, which the closest-point routine leaves exactly 0 / 1 on edges and vertices:
+// two zeros = vertex, one zero = the edge opposite that vertex, none = the face.
+__global__ void k_sign(const float* __restrict__ verts, const int32_t* __restrict__ tris, const float4* __restrict__ snorm,
+                       const float4* __restrict__ vnorm, const float* __restrict__ pts, int64_t n,
+                       const int32_t* __restrict__ tri, const float* __restrict__ bary, float* __restrict__ dist,
+                       int n_tris) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int f = tri[i];
+        if (f < 0 || f >= n_tris) continue;
+        const float b[3] = {bary[3 * i], bary[3 * i + 1], bary[3 * i + 2]};
+        int vi[3];
+        float3 p = make_float3(0.f, 0.f, 0.f);
+        for (int k = 0; k < 3; ++k) {
+            vi[k] = tris[3 * f + k];
+            p.x = fmaf(b[k], verts[3 * vi[k]], p.x);
+            p.y = fmaf(b[k], verts[3 * vi[k] + 1], p.y);
+            p.z = fmaf(b[k], verts[3 * vi[k] + 2], p.z);
+        }
+        const int nz = (b[0] == 0.0f) + (b[1] == 0.0f) + (b[2] == 0.0f);
+        float4 nrm;
+        if (nz >= 2) {
+            const int k = b[0] != 0.0f ? 0 : (b[1] != 0.0f ? 1 : 2);
+            nrm = vnorm[vi[k]];
+        } else if (nz == 1) {
+            const int k = b[0] == 0.0f ? 0 : (b[1] == 0.0f ? 1 : 2);
+            nrm = snorm[4 * (int64_t)f + 1 + (k + 1) % 3];  // edge (v_k+1, v_k+2)
+        } else {
+            nrm = snorm[4 * (int64_t)f];
+        }
+        const float3 q = make_float3(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]);
+        if (dot3(q - p, f3(nrm)) < 0.0f) dist[i] = -dist[i];
+    }
+}
+
 }  // namespace p2m
 
 extern "C" {
+
+int p2m_query_signed(p2m_index* h, const float* d_pts, int64_t n, float* d_sdist, float* d_closest, int32_t* d_tri,
+                     float* d_bary, void* stream) {
+    if (!h || h->meshes.size() != 1) return fail(P2M_ERR_INVALID_ARG, "p2m_query_signed needs a single-mesh index");
+    if (n < 0) return fail(P2M_ERR_INVALID_ARG, "n < 0");
+    if (n == 0) return P2M_OK;
+    if (!d_pts || !d_sdist) return fail(P2M_ERR_INVALID_ARG, "d_pts and d_sdist must be non-NULL");
+    cudaStream_t s = (cudaStream_t)stream;
+    MeshData& m = *h->meshes[0];
+    // the sign needs the triangle and barycentrics: use the caller's buffers or scratch
+    int32_t* tri = d_tri;
+    float* bary = d_bary;
+    if (!tri || !bary) {
+        P2M_TRY(h->sign_scratch.ensure((sizeof(int32_t) + 3 * sizeof(float)) * n + 256));
+        if (!tri) tri = h->sign_scratch.as<int32_t>();
+        if (!bary) bary = reinterpret_cast<float*>(h->sign_scratch.as<char>() + ((sizeof(int32_t) * n + 255) / 256) * 256);
+    }
+    P2M_TRY(run_query(h, m, d_pts, n, d_sdist, d_closest, tri, bary, nullptr, h->scratch_idx, s));
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 32);
+    k_sign<<<blocks, 256, 0, s>>>(m.d_verts.as<float>(), m.d_tris.as<int32_t>(), m.d_snorm.as<float4>(),
+                                  m.d_vnorm.as<float4>(), d_pts, n, tri, bary, d_sdist, (int)m.n_tris);
+    P2M_CUDA_TRY(cudaGetLastError());
+    return P2M_OK;
+}
 
 int p2m_backward(p2m_index* h, const float* d_pts, int64_t n, const int32_t* d_tri, const float* d_bary,
                  const float* d_grad_dist, float* d_grad_pts, float* d_grad_verts, void* stream) {

@@ -118,6 +118,7 @@ struct MeshData {
     std::vector<double> ball_r;       // [B]
     // device
     DevBuf d_verts, d_tris, d_tri, d_tsph, d_tlo, d_thi, d_orig;
+    DevBuf d_snorm, d_vnorm;     // pseudonormals for the sign: [T][4] (face, edges 01/12/20), [V]
     std::vector<int32_t> orig;   // host copy of d_orig
     Bvh bvh;
     DevBuf d_sites, d_refs, d_row_off, d_row_tri, d_row_key, d_cell_off, d_cell_site, d_chunk_off, d_cbox, d_l1_off, d_l1box;
