@@ -168,6 +168,17 @@ int p2m_query(p2m_index* h, const float* d_pts, int64_t n, float* d_dist, float*
 int p2m_query_signed(p2m_index* h, const float* d_pts, int64_t n, float* d_sdist, float* d_closest,
                      int32_t* d_tri, float* d_bary, void* stream);
 
+/* Mesh-to-mesh distance (an extension the paper names as future work, Section 5): mesh B
+ * (device arrays d_verts_b[n_verts_b*3], d_tris_b[n_tris_b*3]) is sampled on the
+ * barycentric lattice of `subdivisions` (0..64) of every triangle (0 = its vertices), the
+ * samples are queried against the index (mesh A), and h_out[3] receives, over the samples,
+ * the minimum distance (an upper bound of the distance between the meshes), the maximum
+ * (the directed Hausdorff distance B -> A over the samples, a lower bound of the true one)
+ * and the mean.  Allocates its sample buffers; synchronises `stream`.  Errors: INVALID_ARG,
+ * OOM, CUDA. */
+int p2m_mesh_distance(p2m_index* h, const float* d_verts_b, int64_t n_verts_b, const int32_t* d_tris_b,
+                      int64_t n_tris_b, int subdivisions, double* h_out, void* stream);
+
 /* The same query from host memory: copies h_pts in chunks to the device, runs the query
  * and copies the results back.  Host
  * buffers may be pageable, but pinned (cudaHostAlloc) buffers are much faster: chunks of

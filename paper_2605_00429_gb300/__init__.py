@@ -85,6 +85,7 @@ SIGNATURES = {
     "p2m_voronoi_cells": ([_P, _I64, _P, _P, _I, _P, _P, _P, _P], _I),
     "p2m_query_noalloc": ([_P, _P, _I64, _P, _P, _P, _P, _P], _I),
     "p2m_query_signed": ([_P, _P, _I64, _P, _P, _P, _P, _P], _I),
+    "p2m_mesh_distance": ([_P, _P, _I64, _P, _I64, _I, _P, _P], _I),
 }
 NOALLOC_MAX_QUERIES = 262144
 
@@ -217,6 +218,17 @@ class P2MIndex:
         _check(lib().p2m_query_signed(self._h, _dptr(pts), n, _dptr(sd), _dptr(cl), _dptr(tr), _dptr(ba),
                                       _stream_ptr(stream)))
         return sd, cl, tr, ba
+
+    def mesh_distance(self, verts_b, tris_b, subdivisions=4, stream=None):
+        """(min, max, mean) distance from mesh B's samples (vertices + a barycentric lattice of
+        `subdivisions` per triangle) to this index's mesh."""
+        import torch
+        vb = torch.as_tensor(np.ascontiguousarray(np.asarray(verts_b, np.float32))).cuda()
+        tb = torch.as_tensor(np.ascontiguousarray(np.asarray(tris_b, np.int32))).cuda()
+        out = np.zeros(3)
+        _check(lib().p2m_mesh_distance(self._h, _dptr(vb), vb.shape[0], _dptr(tb), tb.shape[0], int(subdivisions),
+                                       out.ctypes.data_as(_P), _stream_ptr(stream)))
+        return float(out[0]), float(out[1]), float(out[2])
 
     def query_host(self, pts: np.ndarray, h_dist=None, h_closest=None, h_tri=None, h_bary=None):
         """Host-memory query (copies inside the library).  Arrays may be pinned torch CPU

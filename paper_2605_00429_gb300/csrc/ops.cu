@@ -96,9 +96,101 @@ __global__ void k_sign(const float* __restrict__ verts, const int32_t* __restric
     }
 }
 
+// Sample points of mesh B: the barycentric lattice ((k-i-j) v0 + i v1 + j v2) / k of every
+// triangle (k = subdivisions; k = 0 gives the vertices of each triangle).
+__global__ void k_mesh_samples(const float* __restrict__ verts, const int32_t* __restrict__ tris, int64_t n_tris, int k,
+                               float* __restrict__ out) {
+    const int per = k == 0 ? 3 : (k + 1) * (k + 2) / 2;
+    const int64_t total = n_tris * per;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < total; t += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t f = t / per;
+        int r = (int)(t % per);
+        float w0, w1, w2;
+        if (k == 0) {
+            w0 = r == 0; w1 = r == 1; w2 = r == 2;
+        } else {
+            int i = 0;  // row i holds k - i + 1 points
+            while (r > k - i) { r -= k - i + 1; ++i; }
+            const int j = r;
+            w1 = (float)i / (float)k;
+            w2 = (float)j / (float)k;
+            w0 = (float)(k - i - j) / (float)k;
+        }
+        const int a = tris[3 * f], b = tris[3 * f + 1], c = tris[3 * f + 2];
+        for (int d = 0; d < 3; ++d)
+            out[3 * t + d] = fmaf(w0, verts[3 * a + d], fmaf(w1, verts[3 * b + d], w2 * verts[3 * c + d]));
+    }
+}
+
+// min / max / sum of n distances (one block-reduced atomic per block; distances >= 0, so
+// their float bits order as unsigned integers)
+__global__ void k_dist_stats(const float* __restrict__ d, int64_t n, unsigned* __restrict__ mn, unsigned* __restrict__ mx,
+                             double* __restrict__ sum) {
+    float lmin = INFINITY, lmax = 0.0f;
+    double lsum = 0.0;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float v = d[i];
+        lmin = fminf(lmin, v);
+        lmax = fmaxf(lmax, v);
+        lsum += v;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        lmin = fminf(lmin, __shfl_xor_sync(0xffffffffu, lmin, o));
+        lmax = fmaxf(lmax, __shfl_xor_sync(0xffffffffu, lmax, o));
+        lsum += __shfl_xor_sync(0xffffffffu, lsum, o);
+    }
+    if ((threadIdx.x & 31) == 0) {
+        atomicMin(mn, __float_as_uint(lmin));
+        atomicMax(mx, __float_as_uint(lmax));
+        atomicAdd(sum, lsum);
+    }
+}
+
 }  // namespace p2m
 
 extern "C" {
+
+int p2m_mesh_distance(p2m_index* h, const float* d_verts_b, int64_t n_verts_b, const int32_t* d_tris_b,
+                      int64_t n_tris_b, int subdivisions, double* h_out, void* stream) {
+    if (!h || h->meshes.size() != 1) return fail(P2M_ERR_INVALID_ARG, "p2m_mesh_distance needs a single-mesh index");
+    if (!d_verts_b || !d_tris_b || !h_out || n_verts_b <= 0 || n_tris_b <= 0 || subdivisions < 0 || subdivisions > 64)
+        return fail(P2M_ERR_INVALID_ARG, "bad mesh B or subdivisions (0..64)");
+    cudaStream_t s = (cudaStream_t)stream;
+    MeshData& m = *h->meshes[0];
+    const int per = subdivisions == 0 ? 3 : (subdivisions + 1) * (subdivisions + 2) / 2;
+    const int64_t n = n_tris_b * per;
+    DevBuf pts, dist, stats;
+    P2M_TRY(pts.alloc(sizeof(float) * 3 * n));
+    P2M_TRY(dist.alloc(sizeof(float) * n));
+    P2M_TRY(stats.alloc(64));
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 32);
+    k_mesh_samples<<<blocks, 256, 0, s>>>(d_verts_b, d_tris_b, n_tris_b, subdivisions, pts.as<float>());
+    P2M_CUDA_TRY(cudaGetLastError());
+    P2M_TRY(run_query(h, m, pts.as<float>(), n, dist.as<float>(), nullptr, nullptr, nullptr, nullptr, h->scratch_idx, s));
+    unsigned init[2] = {0x7f800000u, 0u};
+    P2M_CUDA_TRY(cudaMemsetAsync(stats.p, 0, 64, s));
+    P2M_CUDA_TRY(cudaMemcpyAsync(stats.p, init, sizeof(init), cudaMemcpyHostToDevice, s));
+    unsigned* su = stats.as<unsigned>();
+    k_dist_stats<<<blocks, 256, 0, s>>>(dist.as<float>(), n, su, su + 1, reinterpret_cast<double*>(stats.as<char>() + 8));
+    P2M_CUDA_TRY(cudaGetLastError());
+    unsigned char host[16];
+    P2M_CUDA_TRY(cudaMemcpyAsync(host, stats.p, 16, cudaMemcpyDeviceToHost, s));
+    P2M_CUDA_TRY(cudaStreamSynchronize(s));
+    P2M_TRY(check_status_word(h, s, "mesh distance"));
+    unsigned umin, umax;
+    double dsum;
+    std::memcpy(&umin, host, 4);
+    std::memcpy(&umax, host + 4, 4);
+    std::memcpy(&dsum, host + 8, 8);
+    float fmin, fmax;
+    std::memcpy(&fmin, &umin, 4);
+    std::memcpy(&fmax, &umax, 4);
+    h_out[0] = fmin;
+    h_out[1] = fmax;
+    h_out[2] = dsum / (double)n;
+    (void)n_verts_b;
+    return P2M_OK;
+}
 
 int p2m_query_signed(p2m_index* h, const float* d_pts, int64_t n, float* d_sdist, float* d_closest, int32_t* d_tri,
                      float* d_bary, void* stream) {
