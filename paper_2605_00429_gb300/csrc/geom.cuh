@@ -47,12 +47,26 @@ __device__ __forceinline__ TriRec load_tri(const float4* __restrict__ tri, int f
     return t;
 }
 
-// Lower bound |u . (q - v0)| of the distance from q to triangle f (its supporting plane),
-// from the first half of the record.
-__device__ __forceinline__ float tri_plane_dist(const float4* __restrict__ tri, int f, float3 q) {
+// Squared lower bound of the distance from q to triangle f that combines its supporting
+// plane with its bounding sphere sp = (c, r).  Every point p of the triangle lies in the plane
+// and within r of c, so |q - p|^2 = h^2 + |P(q - p)|^2 >= h^2 + max(0, rho - r)^2, with h the
+// plane distance, P the projection onto the plane and rho = |P(q - c)|; this holds wherever
+// c sits relative to the plane.  Near a surface it is much tighter than either bound alone:
+// a triangle whose disc does not reach below q is pruned even when its plane is as close
+// as the answer.  Rounding goes to the safe side: h loses h_slack, and rho^2 loses
+// 4e-6 |q - c|^2 (the unit normal is good to a few ulps in direction and length, so the
+// computed rho^2 is within about 1.5e-6 |q - c|^2 of the exact one).  dc2 = |q - c|^2.  A
+// triangle too thin to project onto has u = 0 and the bound falls back to the sphere's.
+__device__ __forceinline__ float tri_lower_bound2(const float4* __restrict__ tri, int f, float3 q, float4 sp,
+                                                  float dc2, float h_slack) {
     const float4* p = tri + 4 * (int64_t)f;
     const float4 a = __ldg(p), b = __ldg(p + 1);
-    return fabsf(dot3(f3(a), q - f3(b)));
+    const float3 u = f3(a);
+    const float h = fmaxf(fabsf(dot3(u, q - f3(b))) - h_slack, 0.0f);
+    const float hc = dot3(u, q - f3(sp));
+    const float rho2 = fmaf(-4e-6f, dc2, fmaf(-hc, hc, dc2));
+    const float g = fmaxf(sqrtf(fmaxf(rho2, 0.0f)) - sp.w, 0.0f);
+    return fmaf(g, g, h * h);
 }
 
 // Exact squared distance from q to the triangle; (s, t) locate the closest point

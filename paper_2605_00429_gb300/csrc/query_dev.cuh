@@ -115,9 +115,10 @@ __device__ __forceinline__ unsigned long long scan_list(const MeshView& m, float
             const float4 sp = __ldg(m.tsph + f);
             const float dx = q.x - sp.x, dy = q.y - sp.y, dz = q.z - sp.z;
             const float lim = bound + sp.w;
-            if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) > lim * lim) continue;
-            // the supporting plane is a second lower bound, from half of the record
-            if (tri_plane_dist(m.tri, f, q) > bound + 8.0f * m.prune_abs) continue;
+            const float dc2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (dc2 > lim * lim) continue;
+            // plane and sphere together give a second, tighter bound from half of the record
+            if (tri_lower_bound2(m.tri, f, q, sp, dc2, 8.0f * m.prune_abs) > bound * bound) continue;
             if (COUNT) ++n_exact;
             const TriRec T = load_tri(m.tri, f);
             float s, t;
@@ -198,8 +199,8 @@ __device__ __forceinline__ bool warp_scan_list(const MeshView& m, float3 q, int 
             const float4 sp = __ldg(m.tsph + f);
             const float dx = q.x - sp.x, dy = q.y - sp.y, dz = q.z - sp.z;
             const float lim = bound + sp.w;
-            if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) <= lim * lim &&
-                tri_plane_dist(m.tri, f, q) <= bound + 8.0f * m.prune_abs) {
+            const float dc2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            if (dc2 <= lim * lim && tri_lower_bound2(m.tri, f, q, sp, dc2, 8.0f * m.prune_abs) <= bound * bound) {
                 if (COUNT) ++n_exact;
                 const TriRec T = load_tri(m.tri, f);
                 const float d2 = tri_dist2(q, T, s, t);
