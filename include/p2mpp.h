@@ -76,13 +76,15 @@ typedef struct {
     /* Query schedule [0]: 0 = queries sorted by the Morton code of their grid cell, then
      * thread per query for lists up to long_list entries and a warp-cooperative best-first
      * scan for longer lists; 1 = thread per query for every list; 2 = warp per query for
-     * every list; 3 = as 0 without the sort.  All give identical results. */
+     * every list; 3 = as 0 without the sort; 4 = as 0, with the queries regrouped by
+     * nearest site (a second radix sort) before the list scan.  All give identical
+     * results. */
     int schedule;
     /* Deterministic vertex-gradient accumulation (fixed-point integer atomics) [1]. */
     int deterministic;
     /* Seed of the site jitter used to break exact Delaunay degeneracies [1]. */
     int seed;
-    /* Lists longer than this take the warp-cooperative scan in schedules 0 and 3; 0 picks
+    /* Lists longer than this take the warp-cooperative scan in schedules 0, 3 and 4; 0 picks
      * the default (256) [0]. */
     int long_list;
 } p2m_build_params;

@@ -142,7 +142,7 @@ static int validate_params(const p2m_build_params& p) {
     if (!(p.ring_radius_scale > 0.0f)) return fail(P2M_ERR_INVALID_ARG, "ring_radius_scale must be > 0");
     if (!(p.build_eps_rel >= 0.0f && p.build_eps_rel < 1e-2f)) return fail(P2M_ERR_INVALID_ARG, "build_eps_rel out of range");
     if (p.nn_grid_res < 0 || p.nn_grid_res > 1024) return fail(P2M_ERR_INVALID_ARG, "nn_grid_res out of range");
-    if (p.schedule < 0 || p.schedule > 3) return fail(P2M_ERR_INVALID_ARG, "schedule must be 0..3");
+    if (p.schedule < 0 || p.schedule > 4) return fail(P2M_ERR_INVALID_ARG, "schedule must be 0..4");
     if (p.long_list < 0) return fail(P2M_ERR_INVALID_ARG, "long_list must be >= 0");
     return P2M_OK;
 }
@@ -301,11 +301,13 @@ static int build_mesh(MeshData& m, const p2m_build_params& prm, p2m_index* h, cu
     st.ms_lbvh = t3 - t2;
     // list-scan schedule: 1 = thread per query for every list, 2 = warp per query for every
     // list, 0/3 = thread per query for lists up to long_list entries and warp per query beyond;
-    // 0 also processes the queries in grid-cell Morton order.  Known before the lists are
-    // built: the lists scanned per thread are stored ordered by their lower bound.
+    // 0 also processes the queries in grid-cell Morton order, and 4 then regroups them by
+    // nearest site.  Known before the lists are built: the lists scanned per thread are
+    // stored ordered by their lower bound.
     const int long_list = prm.long_list > 0 ? prm.long_list : 256;
     m.long_row = prm.schedule == 1 ? 0x7fffffff : (prm.schedule == 2 ? 0 : long_list);
-    m.sorted = prm.schedule == 0;
+    m.sorted = prm.schedule == 0 || prm.schedule == 4;
+    m.site_sorted = prm.schedule == 4;
     // host Voronoi, augmentation, corner balls, lists, nearest-site grid
     P2M_TRY(build_partition(m, prm, h, s));
     st.ms_total = now_ms() - t0;

@@ -125,6 +125,7 @@ struct MeshData {
     int64_t nnz = 0, n_chunks = 0;
     int long_row = 256;
     bool sorted = true;          // process queries in grid-cell Morton order
+    bool site_sorted = false;    // then regroup them by nearest site before the list scan
     int G = 0;
     float3 g_lo{}, g_hi{}, g_inv_h{};
     p2m_stats stats{};

@@ -25,11 +25,20 @@ __global__ void __launch_bounds__(256) k_query_thread(MeshView m, const float* _
                                                      int32_t* __restrict__ tri_out, float* __restrict__ bary,
                                                      int32_t* __restrict__ rest, int* __restrict__ n_rest,
                                                      int2* __restrict__ longq, int* __restrict__ n_long,
-                                                     unsigned long long* counters, const int32_t* __restrict__ perm,
-                                                     int2* __restrict__ cand, unsigned char* __restrict__ flag) {
+                                                     unsigned long long* counters, const float4* __restrict__ qs,
+                                                     int2* __restrict__ cand, unsigned char* __restrict__ flag,
+                                                     float4* __restrict__ rec) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t i = perm ? (int64_t)__ldg(perm + k) : k;
-        const float3 q = make_float3(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]);
+        // sorted order: the points were gathered into qs (xyz, index); else input order
+        int64_t i = k;
+        float3 q;
+        if (qs) {
+            const float4 p = __ldg(qs + k);
+            i = __float_as_int(p.w);
+            q = make_float3(p.x, p.y, p.z);
+        } else {
+            q = make_float3(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]);
+        }
         int cell;
         int site = -1;
         if (grid_cell(m, q, cell)) site = nearest_site<COUNT>(m, q, cell, counters);
@@ -51,7 +60,93 @@ __global__ void __launch_bounds__(256) k_query_thread(MeshView m, const float* _
             if (COUNT) atomicAdd(counters + C_OUTSIDE, 1ull);
             continue;
         }
-        write_result(m, i, key, s, t, dist, closest, tri_out, bary);
+        if (rec) write_record(m, rec, i, key, s, t);
+        else write_result(m, i, key, s, t, dist, closest, tri_out, bary);
+    }
+}
+
+// Sorted order, first step: the points in sorted order with their index in .w, so that the
+// query kernels read them coalesced (the random gather runs here, in a streaming kernel).
+__global__ void k_gather_points(const float* __restrict__ pts, const int32_t* __restrict__ perm, int64_t n,
+                                float4* __restrict__ qs) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t i = __ldg(perm + k);
+        qs[k] = make_float4(__ldg(pts + 3 * i), __ldg(pts + 3 * i + 1), __ldg(pts + 3 * i + 2), __int_as_float((int)i));
+    }
+}
+
+// Sorted order, last step: the 32-byte result records (in input order) to the output arrays,
+// coalesced.  Queries left to the BVH search have no record; that search runs afterwards and
+// overwrites their outputs.
+__global__ void k_split_records(const float4* __restrict__ rec, int64_t n, float* __restrict__ dist,
+                                float* __restrict__ closest, int32_t* __restrict__ tri_out, float* __restrict__ bary) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float4 a = __ldcs(rec + 2 * i), b = __ldcs(rec + 2 * i + 1);
+        dist[i] = a.x;
+        if (closest) {
+            closest[3 * i] = a.y;
+            closest[3 * i + 1] = a.z;
+            closest[3 * i + 2] = a.w;
+        }
+        if (tri_out) tri_out[i] = __float_as_int(b.x);
+        if (bary) {
+            bary[3 * i] = b.y;
+            bary[3 * i + 1] = b.z;
+            bary[3 * i + 2] = b.w;
+        }
+    }
+}
+
+// Site-sorted schedule, first pass: the nearest site of every query, taken in Morton order
+// (so the grid lookups of neighbouring threads hit the same cells).  The site becomes the key
+// of a second radix sort that gathers the queries of each site together (the value is the
+// Morton-order position); points outside the domain box get the key n_sites and sort last.
+template <bool COUNT>
+__global__ void __launch_bounds__(256) k_query_sites(MeshView m, const float4* __restrict__ qs, int64_t n,
+                                                    unsigned* __restrict__ skey, int32_t* __restrict__ sval,
+                                                    unsigned long long* counters) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const float4 p = __ldg(qs + k);
+        const float3 q = make_float3(p.x, p.y, p.z);
+        int cell;
+        int site = -1;
+        if (grid_cell(m, q, cell)) site = nearest_site<COUNT>(m, q, cell, counters);
+        skey[k] = site >= 0 ? (unsigned)site : (unsigned)m.n_sites;
+        sval[k] = (int32_t)k;
+    }
+}
+
+// Site-sorted schedule, second pass: thread per query over the queries grouped by site, so
+// the lanes of a warp mostly scan the same interception list (its entries, spheres and
+// triangle records are loaded once for the warp, and trip counts are alike).  Long lists are
+// flagged for the order-preserving compaction, as in the Morton-ordered schedule.
+template <bool COUNT>
+__global__ void __launch_bounds__(256) k_query_scan(MeshView m, const float4* __restrict__ qbuf,
+                                                   const unsigned* __restrict__ skey, const int32_t* __restrict__ sval,
+                                                   int64_t n, float* __restrict__ dist, float* __restrict__ closest,
+                                                   int32_t* __restrict__ tri_out, float* __restrict__ bary,
+                                                   int32_t* __restrict__ rest, int* __restrict__ n_rest,
+                                                   int2* __restrict__ cand, unsigned char* __restrict__ flag,
+                                                   unsigned long long* counters, float4* __restrict__ rec) {
+    for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+        const float4 p = __ldg(qbuf + __ldg(sval + k));
+        const int i = __float_as_int(p.w);
+        const float3 q = make_float3(p.x, p.y, p.z);
+        const unsigned sk = __ldg(skey + k);
+        const int site = sk < (unsigned)m.n_sites ? (int)sk : -1;
+        const bool is_long = site >= 0 && __ldg(m.row_off + site + 1) - __ldg(m.row_off + site) > m.long_row;
+        flag[k] = is_long;
+        cand[k] = make_int2(i, site);
+        if (is_long) continue;
+        unsigned long long key = ~0ull;
+        float s = 0.0f, t = 0.0f;
+        if (site >= 0) key = scan_list<COUNT>(m, q, site, s, t, counters);
+        if (key == ~0ull) {
+            rest[atomicAdd(n_rest, 1)] = (int32_t)i;
+            if (COUNT) atomicAdd(counters + C_OUTSIDE, 1ull);
+            continue;
+        }
+        write_record(m, rec, i, key, s, t);
     }
 }
 
@@ -66,7 +161,7 @@ __device__ __forceinline__ void warp_query_one(const MeshView& m, const float* _
                                                float* __restrict__ dist, float* __restrict__ closest,
                                                int32_t* __restrict__ tri_out, float* __restrict__ bary,
                                                int32_t* __restrict__ rest, int* __restrict__ n_rest,
-                                               unsigned long long* counters) {
+                                               unsigned long long* counters, float4* __restrict__ rec) {
     const int64_t i = qs.x;
     const float3 q = make_float3(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]);
     unsigned bhi, blo;
@@ -74,6 +169,7 @@ __device__ __forceinline__ void warp_query_one(const MeshView& m, const float* _
     const bool found = warp_scan_list<COUNT>(m, q, qs.y, bhi, blo, bs, bt, counters);
     if ((threadIdx.x & 31) == 0) {
         if (!found) rest[atomicAdd(n_rest, 1)] = (int32_t)i;
+        else if (rec) write_record(m, rec, i, ((unsigned long long)bhi << 32) | blo, bs, bt);
         else write_result(m, i, ((unsigned long long)bhi << 32) | blo, bs, bt, dist, closest, tri_out, bary);
     }
 }
@@ -84,12 +180,13 @@ __global__ void __launch_bounds__(256) k_query_warp(MeshView m, const float* __r
                                                    float* __restrict__ dist, float* __restrict__ closest,
                                                    int32_t* __restrict__ tri_out, float* __restrict__ bary,
                                                    int32_t* __restrict__ rest, int* __restrict__ n_rest,
-                                                   unsigned long long* counters, int* __restrict__ head) {
+                                                   unsigned long long* counters, int* __restrict__ head,
+                                                   float4* __restrict__ rec) {
     const int nq = *n_long;
     if (!head) {
         const int nwarps = (gridDim.x * blockDim.x) >> 5;
         for (int k = (blockIdx.x * blockDim.x + threadIdx.x) >> 5; k < nq; k += nwarps)
-            warp_query_one<COUNT>(m, pts, longq[k], dist, closest, tri_out, bary, rest, n_rest, counters);
+            warp_query_one<COUNT>(m, pts, longq[k], dist, closest, tri_out, bary, rest, n_rest, counters, rec);
         return;
     }
     __shared__ int s_base, s_next;
@@ -107,7 +204,8 @@ __global__ void __launch_bounds__(256) k_query_warp(MeshView m, const float* __r
             if (lane == 0) j = atomicAdd(&s_next, 1);
             j = __shfl_sync(0xffffffffu, j, 0);
             if (j >= kSeg || base + j >= nq) break;
-            warp_query_one<COUNT>(m, pts, longq[base + j], dist, closest, tri_out, bary, rest, n_rest, counters);
+            warp_query_one<COUNT>(m, pts, longq[base + j], dist, closest, tri_out, bary, rest, n_rest, counters,
+                                  rec);
         }
         __syncthreads();  // the run is finished before s_base changes
     }
@@ -154,21 +252,31 @@ int run_query(p2m_index* h, MeshData& m, const float* d_pts, int64_t n, float* d
               int32_t* d_tri, float* d_bary, unsigned long long* counters, DevBuf& rest, cudaStream_t s) {
     const MeshView v = m.view();
     if (v.G == 0) return launch_bvh_closest(v, d_pts, nullptr, nullptr, n, d_dist, d_closest, d_tri, d_bary, index_status(h), s);
-    // scratch: rest ids [n], long queue [n] of int2, counters, and for the sorted schedule the
-    // sort keys / permutation double buffers, per-query (query, site) pairs and long flags,
-    // and the temporary storage of the radix sort and of the compaction
+    // scratch: rest ids [n], long queue [n] of int2, counters; for the sorted schedules also
+    // the sort keys / permutation double buffers [4][n], per-query (query, site) pairs and long
+    // flags, the temporary storage of the radix sorts and of the compaction, the points in
+    // sorted order [n] float4 and the result records [n][2] float4
     const bool sorted = m.sorted && n >= 4096 && n <= 0x7fffffff;
+    const bool by_site = sorted && m.site_sorted;
+    int site_bits = 1;
+    while ((1u << site_bits) <= (unsigned)v.n_sites) ++site_bits;  // keys 0..n_sites
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
     const size_t rest_bytes = up(sizeof(int32_t) * n), long_bytes = up(sizeof(int2) * n), cnt_bytes = 256;
     size_t sort_tmp = 0, sel_tmp = 0;
     if (sorted) {
         P2M_CUDA_TRY(cub::DeviceRadixSort::SortPairs(nullptr, sort_tmp, (unsigned*)nullptr, (unsigned*)nullptr,
                                                      (int32_t*)nullptr, (int32_t*)nullptr, (int)n, 0, 24, s));
+        size_t site_tmp = 0;
+        P2M_CUDA_TRY(cub::DeviceRadixSort::SortPairs(nullptr, site_tmp, (unsigned*)nullptr, (unsigned*)nullptr,
+                                                     (int32_t*)nullptr, (int32_t*)nullptr, (int)n, 0, site_bits, s));
+        sort_tmp = std::max(sort_tmp, site_tmp);
         P2M_CUDA_TRY(cub::DeviceSelect::Flagged(nullptr, sel_tmp, (int2*)nullptr, (unsigned char*)nullptr, (int2*)nullptr,
                                                 (int*)nullptr, (int)n, s));
     }
-    const size_t a4 = up(sizeof(int32_t) * n);
-    const size_t sort_bytes = sorted ? 4 * a4 + up(sizeof(int2) * n) + up(n) + up(std::max(sort_tmp, sel_tmp)) : 0;
+    const size_t a4 = up(sizeof(int32_t) * n), tmp_bytes = up(std::max(sort_tmp, sel_tmp));
+    const size_t sort_bytes = sorted ? 4 * a4 + up(sizeof(int2) * n) + up(n) + tmp_bytes + up(sizeof(float4) * n) +
+                                           up(2 * sizeof(float4) * n)
+                                     : 0;
     P2M_TRY(rest.ensure(rest_bytes + long_bytes + cnt_bytes + sort_bytes));
     char* base = rest.as<char>();
     int32_t* d_rest = reinterpret_cast<int32_t*>(base);
@@ -178,47 +286,82 @@ int run_query(p2m_index* h, MeshData& m, const float* d_pts, int64_t n, float* d
     const int threads = 256;
     const int blocks = query_grid_blocks(n, threads);
     const int wblocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, 152LL * 16));
-    const int32_t* perm = nullptr;
-    int2* cand = nullptr;
-    unsigned char* flag = nullptr;
-    void* sel_buf = nullptr;
+    int* head = nullptr;
+    float4* rec = nullptr;
     if (sorted) {
         char* sb = base + rest_bytes + long_bytes + cnt_bytes;
         unsigned* k0 = reinterpret_cast<unsigned*>(sb);
         unsigned* k1 = reinterpret_cast<unsigned*>(sb + a4);
         int32_t* i0 = reinterpret_cast<int32_t*>(sb + 2 * a4);
         int32_t* i1 = reinterpret_cast<int32_t*>(sb + 3 * a4);
-        cand = reinterpret_cast<int2*>(sb + 4 * a4);
-        flag = reinterpret_cast<unsigned char*>(sb + 4 * a4 + up(sizeof(int2) * n));
-        sel_buf = sb + 4 * a4 + up(sizeof(int2) * n) + up(n);
+        char* p = sb + 4 * a4;
+        int2* cand = reinterpret_cast<int2*>(p);
+        p += up(sizeof(int2) * n);
+        unsigned char* flag = reinterpret_cast<unsigned char*>(p);
+        p += up(n);
+        void* tmp = p;
+        p += tmp_bytes;
+        float4* qs = reinterpret_cast<float4*>(p);
+        p += up(sizeof(float4) * n);
+        rec = reinterpret_cast<float4*>(p);
         k_query_keys<<<blocks, threads, 0, s>>>(v, d_pts, n, k0, i0);
         P2M_CUDA_TRY(cudaGetLastError());
         cub::DoubleBuffer<unsigned> dk(k0, k1);
         cub::DoubleBuffer<int32_t> dv(i0, i1);
-        P2M_CUDA_TRY(cub::DeviceRadixSort::SortPairs(sel_buf, sort_tmp, dk, dv, (int)n, 0, 24, s));
-        perm = dv.Current();
-    }
-    if (counters)
-        k_query_thread<true><<<blocks, threads, 0, s>>>(v, d_pts, n, d_dist, d_closest, d_tri, d_bary, d_rest, d_cnt,
-                                                        d_long, d_cnt + 1, counters, perm, cand, flag);
-    else
-        k_query_thread<false><<<blocks, threads, 0, s>>>(v, d_pts, n, d_dist, d_closest, d_tri, d_bary, d_rest, d_cnt,
-                                                         d_long, d_cnt + 1, nullptr, perm, cand, flag);
-    P2M_CUDA_TRY(cudaGetLastError());
-    int* head = nullptr;
-    if (sorted) {
+        P2M_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp, sort_tmp, dk, dv, (int)n, 0, 24, s));
+        k_gather_points<<<blocks, threads, 0, s>>>(d_pts, dv.Current(), n, qs);
+        P2M_CUDA_TRY(cudaGetLastError());
+        if (by_site) {
+            // nearest sites in Morton order, then a stable sort by site (the Morton keys and the
+            // permutation are dead once the points are gathered)
+            unsigned* sk = dk.Alternate();
+            int32_t* sv = dv.Alternate();
+            if (counters)
+                k_query_sites<true><<<blocks, threads, 0, s>>>(v, qs, n, sk, sv, counters);
+            else
+                k_query_sites<false><<<blocks, threads, 0, s>>>(v, qs, n, sk, sv, nullptr);
+            P2M_CUDA_TRY(cudaGetLastError());
+            cub::DoubleBuffer<unsigned> sk2(sk, dk.Current());
+            cub::DoubleBuffer<int32_t> sv2(sv, dv.Current());
+            P2M_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp, sort_tmp, sk2, sv2, (int)n, 0, site_bits, s));
+            if (counters)
+                k_query_scan<true><<<blocks, threads, 0, s>>>(v, qs, sk2.Current(), sv2.Current(), n, d_dist, d_closest,
+                                                             d_tri, d_bary, d_rest, d_cnt, cand, flag, counters, rec);
+            else
+                k_query_scan<false><<<blocks, threads, 0, s>>>(v, qs, sk2.Current(), sv2.Current(), n, d_dist, d_closest,
+                                                              d_tri, d_bary, d_rest, d_cnt, cand, flag, nullptr, rec);
+        } else if (counters) {
+            k_query_thread<true><<<blocks, threads, 0, s>>>(v, d_pts, n, d_dist, d_closest, d_tri, d_bary, d_rest, d_cnt,
+                                                            d_long, d_cnt + 1, counters, qs, cand, flag, rec);
+        } else {
+            k_query_thread<false><<<blocks, threads, 0, s>>>(v, d_pts, n, d_dist, d_closest, d_tri, d_bary, d_rest, d_cnt,
+                                                             d_long, d_cnt + 1, nullptr, qs, cand, flag, rec);
+        }
+        P2M_CUDA_TRY(cudaGetLastError());
         // order-preserving compaction of the long queries (count written on the device)
-        P2M_CUDA_TRY(cub::DeviceSelect::Flagged(sel_buf, sel_tmp, cand, flag, d_long, d_cnt + 1, (int)n, s));
+        P2M_CUDA_TRY(cub::DeviceSelect::Flagged(tmp, sel_tmp, cand, flag, d_long, d_cnt + 1, (int)n, s));
         head = d_cnt + 2;
+    } else if (counters) {
+        k_query_thread<true><<<blocks, threads, 0, s>>>(v, d_pts, n, d_dist, d_closest, d_tri, d_bary, d_rest, d_cnt,
+                                                        d_long, d_cnt + 1, counters, nullptr, nullptr, nullptr, nullptr);
+    } else {
+        k_query_thread<false><<<blocks, threads, 0, s>>>(v, d_pts, n, d_dist, d_closest, d_tri, d_bary, d_rest, d_cnt,
+                                                         d_long, d_cnt + 1, nullptr, nullptr, nullptr, nullptr, nullptr);
     }
+    P2M_CUDA_TRY(cudaGetLastError());
     if (counters)
         k_query_warp<true><<<wblocks, threads, 0, s>>>(v, d_pts, d_long, d_cnt + 1, d_dist, d_closest, d_tri, d_bary,
-                                                       d_rest, d_cnt, counters, head);
+                                                       d_rest, d_cnt, counters, head, rec);
     else
         k_query_warp<false><<<wblocks, threads, 0, s>>>(v, d_pts, d_long, d_cnt + 1, d_dist, d_closest, d_tri, d_bary,
-                                                        d_rest, d_cnt, nullptr, head);
+                                                        d_rest, d_cnt, nullptr, head, rec);
     P2M_CUDA_TRY(cudaGetLastError());
-    // the points left over take the exact BVH search; the count stays on the device
+    if (rec) {
+        k_split_records<<<blocks, threads, 0, s>>>(rec, n, d_dist, d_closest, d_tri, d_bary);
+        P2M_CUDA_TRY(cudaGetLastError());
+    }
+    // the points left over take the exact BVH search (after the split, which leaves their
+    // outputs undefined); the count stays on the device
     return launch_bvh_closest(v, d_pts, d_rest, d_cnt, n, d_dist, d_closest, d_tri, d_bary, index_status(h), s);
 }
 
@@ -246,9 +389,9 @@ int launch_query_on_scratch(p2m_index* h, MeshData& m, const float* d_pts, int64
     const int blocks = query_grid_blocks(n, threads);
     const int wblocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, 152LL * 16));
     k_query_thread<false><<<blocks, threads, 0, s>>>(v, d_pts, n, d_dist, d_closest, d_tri, d_bary, d_rest, d_cnt, d_long,
-                                                     d_cnt + 1, nullptr, nullptr, nullptr, nullptr);
+                                                     d_cnt + 1, nullptr, nullptr, nullptr, nullptr, nullptr);
     k_query_warp<false><<<wblocks, threads, 0, s>>>(v, d_pts, d_long, d_cnt + 1, d_dist, d_closest, d_tri, d_bary, d_rest,
-                                                    d_cnt, nullptr, nullptr);
+                                                    d_cnt, nullptr, nullptr, nullptr);
     P2M_CUDA_TRY(cudaGetLastError());
     return launch_bvh_closest(v, d_pts, d_rest, d_cnt, n, d_dist, d_closest, d_tri, d_bary, index_status(h), s);
 }

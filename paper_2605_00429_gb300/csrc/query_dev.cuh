@@ -159,6 +159,19 @@ __device__ __forceinline__ void write_result(const MeshView& m, int64_t i, unsig
     }
 }
 
+// The same result as one 32-byte record at rec[2i .. 2i+1]: (distance, closest point) and
+// (original triangle id bits, barycentrics).  Queries taken in sorted order land at random
+// indices; a record fills one whole 32-byte sector, where the four separate outputs would
+// each touch a partial sector.  k_split_records turns the records into the output arrays.
+__device__ __forceinline__ void write_record(const MeshView& m, float4* __restrict__ rec, int64_t i,
+                                             unsigned long long key, float s, float t) {
+    const int f = (int)(key & 0xffffffffu);
+    const TriRec T = load_tri(m.tri, f);
+    const float3 p = tri_point(T, s, t);
+    rec[2 * i] = make_float4(sqrtf(__uint_as_float((unsigned)(key >> 32))), p.x, p.y, p.z);
+    rec[2 * i + 1] = make_float4(__int_as_float(__ldg(m.orig + f)), 1.0f - s - t, s, t);
+}
+
 __device__ __forceinline__ float box2_dist2(const float4* __restrict__ box, int64_t k, float3 q) {
     const float4 lo = __ldg(box + 2 * k), hi = __ldg(box + 2 * k + 1);
     return box_dist2(q, f3(lo), f3(hi));

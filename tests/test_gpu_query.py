@@ -169,7 +169,7 @@ def test_counters(p2m):
     assert c["site_candidates"] >= 20000 - c["n_outside"]
 
 
-@pytest.mark.parametrize("schedule", [1, 2, 3])
+@pytest.mark.parametrize("schedule", [1, 2, 3, 4])
 def test_schedules_agree(p2m, schedule):
     """Thread-per-query, warp-per-query and the mixed schedule give the same answers."""
     mesh, q = W.workload_large(50_000, k=4)
