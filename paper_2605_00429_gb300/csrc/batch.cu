@@ -31,7 +31,8 @@ struct BatchArgs {
     int4* longq;        // (query, site, mesh, 0)
     int2* rest;         // (query, mesh)
     int* ctr;           // [0] tile head, [1] long count, [2] rest count, [3] long head
-    const int32_t* perm;  // sorted position -> query (NULL: unsorted)
+    const float4* qs;   // sorted order: the points with their index in .w (NULL: unsorted)
+    float4* rec;        // sorted order: 32-byte result records, split after the warp pass
 };
 
 __global__ void __launch_bounds__(256) k_batch_thread(BatchArgs a) {
@@ -45,8 +46,15 @@ __global__ void __launch_bounds__(256) k_batch_thread(BatchArgs a) {
         const int4 tile = __ldg(a.tiles + t);
         const MeshView& m = a.views[tile.x];
         for (int64_t k = (int64_t)tile.y + threadIdx.x; k < tile.z; k += blockDim.x) {
-            const int64_t i = a.perm ? (int64_t)__ldg(a.perm + k) : k;
-            const float3 q = make_float3(a.pts[3 * i], a.pts[3 * i + 1], a.pts[3 * i + 2]);
+            int64_t i = k;
+            float3 q;
+            if (a.qs) {
+                const float4 p = __ldg(a.qs + k);
+                i = __float_as_int(p.w);
+                q = make_float3(p.x, p.y, p.z);
+            } else {
+                q = make_float3(a.pts[3 * i], a.pts[3 * i + 1], a.pts[3 * i + 2]);
+            }
             int cell;
             int site = -1;
             if (m.G > 0 && grid_cell(m, q, cell)) site = nearest_site<false>(m, q, cell, nullptr);
@@ -61,7 +69,8 @@ __global__ void __launch_bounds__(256) k_batch_thread(BatchArgs a) {
                 a.rest[atomicAdd(a.ctr + 2, 1)] = make_int2((int)i, tile.x);
                 continue;
             }
-            write_result(m, i, key, s, tt, a.dist, a.closest, a.tri, a.bary);
+            if (a.rec) write_record(m, a.rec, i, key, s, tt);
+            else write_result(m, i, key, s, tt, a.dist, a.closest, a.tri, a.bary);
         }
     }
 }
@@ -83,6 +92,7 @@ __global__ void __launch_bounds__(256, 2) k_batch_warp(BatchArgs a) {
         const bool found = warp_scan_list<false>(m, q, e.y, bhi, blo, bs, bt, nullptr);
         if (lane == 0) {
             if (!found) a.rest[atomicAdd(a.ctr + 2, 1)] = make_int2((int)i, e.z);
+            else if (a.rec) write_record(m, a.rec, i, ((unsigned long long)bhi << 32) | blo, bs, bt);
             else write_result(m, i, ((unsigned long long)bhi << 32) | blo, bs, bt, a.dist, a.closest, a.tri, a.bary);
         }
     }
@@ -154,10 +164,17 @@ static int launch_batch(BatchState& b, const BatchArgs& a0, unsigned* status, cu
         cub::DoubleBuffer<int32_t> dv(i0, i0 + N);
         size_t tb = b.sort_tmp_bytes;
         P2M_CUDA_TRY(cub::DeviceRadixSort::SortPairs(b.sort_tmp.p, tb, dk, dv, (int)N, 0, b.sort_end_bit, s));
-        a.perm = dv.Current();
+        // the points in sorted order; results go out as whole-sector records, split below
+        P2M_TRY(launch_gather_points(a.pts, dv.Current(), N, b.qs.as<float4>(), s));
+        a.qs = b.qs.as<const float4>();
+        a.rec = b.rec.as<float4>();
     }
     k_batch_thread<<<b.grid_thread, 256, 0, s>>>(a);
     k_batch_warp<<<b.grid_warp, 256, 0, s>>>(a);
+    P2M_CUDA_TRY(cudaGetLastError());
+    // queries left to the BVH search have no record: the split leaves their outputs undefined
+    // and the BVH pass writes them afterwards
+    if (a.rec) P2M_TRY(launch_split_records(a.rec, b.offsets.back(), a.dist, a.closest, a.tri, a.bary, s));
     k_batch_bvh<<<b.grid_bvh, 128, 0, s>>>(a, status);
     P2M_CUDA_TRY(cudaGetLastError());
     return P2M_OK;
@@ -227,6 +244,8 @@ int run_batch_query(p2m_index* h, const float* d_pts, const int64_t* h_off, floa
                                                      (int32_t*)nullptr, (int32_t*)nullptr, (int)N, 0, b.sort_end_bit, s));
         P2M_TRY(b.sort_tmp.ensure(tb + 16));
         b.sort_tmp_bytes = tb;
+        P2M_TRY(b.qs.ensure(sizeof(float4) * N));
+        P2M_TRY(b.rec.ensure(2 * sizeof(float4) * N));
     }
     BatchArgs a;
     a.views = b.views.as<const MeshView>();
@@ -238,7 +257,8 @@ int run_batch_query(p2m_index* h, const float* d_pts, const int64_t* h_off, floa
     a.longq = b.longq.as<int4>();
     a.rest = b.rest.as<int2>();
     a.ctr = b.counter.as<int>();
-    a.perm = nullptr;
+    a.qs = nullptr;
+    a.rec = nullptr;
     unsigned* status = index_status(h);
     if (!b.tuned) {
         // autotuner: time each (tile, long_row) candidate on this batch, keep the fastest

@@ -19,6 +19,7 @@ struct BatchState {
     DevBuf counter;      // tile head, long count, rest count, long head
     DevBuf longq, rest;  // queues of the warp pass and of the BVH pass
     DevBuf sort_keys, sort_idx, sort_tmp;  // per-mesh Morton sort of the queries
+    DevBuf qs, rec;      // points in sorted order, 32-byte result records
     size_t sort_tmp_bytes = 0;
     int sort_end_bit = 24;
     int n_tiles = 0;

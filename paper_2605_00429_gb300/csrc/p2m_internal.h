@@ -148,6 +148,12 @@ int tri_boxes(const float* d_verts, const int32_t* d_tris, int n_tris, float4* l
 // K5: exact closest triangle by BVH branch and bound.  Queries are d_pts[d_idx[k]] for
 // k < *d_count (both on the device) when d_idx is given, else d_pts[k] for k < n.  n bounds
 // the launch either way.
+// Sorted-order helpers of the query path: qs[k] = (pts[perm[k]], perm[k] bits); and the
+// 32-byte result records rec[2i..2i+1] split into the output arrays (closest, tri, bary may be
+// NULL).
+int launch_gather_points(const float* d_pts, const int32_t* d_perm, int64_t n, float4* d_qs, cudaStream_t s);
+int launch_split_records(const float4* d_rec, int64_t n, float* d_dist, float* d_closest, int32_t* d_tri,
+                         float* d_bary, cudaStream_t s);
 int launch_bvh_closest(const MeshView& m, const float* d_pts, const int32_t* d_idx, const int* d_count,
                        int64_t n, float* d_dist, float* d_closest, int32_t* d_tri, float* d_bary,
                        unsigned* d_status, cudaStream_t s);

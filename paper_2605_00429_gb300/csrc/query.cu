@@ -365,6 +365,21 @@ int run_query(p2m_index* h, MeshData& m, const float* d_pts, int64_t n, float* d
     return launch_bvh_closest(v, d_pts, d_rest, d_cnt, n, d_dist, d_closest, d_tri, d_bary, index_status(h), s);
 }
 
+int launch_gather_points(const float* d_pts, const int32_t* d_perm, int64_t n, float4* d_qs, cudaStream_t s) {
+    if (n <= 0) return P2M_OK;
+    k_gather_points<<<query_grid_blocks(n, 256), 256, 0, s>>>(d_pts, d_perm, n, d_qs);
+    P2M_CUDA_TRY(cudaGetLastError());
+    return P2M_OK;
+}
+
+int launch_split_records(const float4* d_rec, int64_t n, float* d_dist, float* d_closest, int32_t* d_tri,
+                         float* d_bary, cudaStream_t s) {
+    if (n <= 0) return P2M_OK;
+    k_split_records<<<query_grid_blocks(n, 256), 256, 0, s>>>(d_rec, n, d_dist, d_closest, d_tri, d_bary);
+    P2M_CUDA_TRY(cudaGetLastError());
+    return P2M_OK;
+}
+
 int run_nearest_site(p2m_index* h, MeshData& m, const float* d_pts, int64_t n, int32_t* d_site, cudaStream_t s) {
     (void)h;
     const MeshView v = m.view();
