@@ -351,7 +351,7 @@ def main():
             "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},
             "csr_build_ms": st["ms_tri"] + st["ms_lbvh"] + st["ms_k1"],
             "build": {"wall_ms": build_wall_ms, "host_delaunay_ms": st["ms_delaunay"], "host_aug_ms": st["ms_aug"],
-                      "host_cells_ms": st["ms_cells"], "gpu_lists_ms": st["ms_k1"], "gpu_grid_ms": st["ms_grid"],
+                      "gpu_cells_ms": st["ms_cells"], "cells_clipped_on_host": st["n_cells_host"], "gpu_lists_ms": st["ms_k1"], "gpu_grid_ms": st["ms_grid"],
                       "sites": st["n_sites"], "aux_sites": st["n_aux_sites"], "nnz": st["nnz"],
                       "max_list": st["max_row"], "avg_list": st["avg_row"], "grid": st["grid_res"]},
             "counters": {"queried_entries": cnt["row_entries"] / n, "queried_exact": cnt["exact_tests"] / n,

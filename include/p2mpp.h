@@ -87,6 +87,9 @@ typedef struct {
     /* Lists longer than this take the warp-cooperative scan in schedules 0, 3 and 4; 0 picks
      * the default (256) [0]. */
     int long_list;
+    /* Clip the Voronoi cells on the GPU in FP64 [1]; cells beyond the device clipper's fixed
+     * capacity (58 cutting planes) are clipped on the host.  0 = every cell on the host. */
+    int gpu_cells;
 } p2m_build_params;
 
 /* Build statistics (Section 4.1, Table 1: Max / Avg list length) and stage timings. */
@@ -108,6 +111,10 @@ typedef struct {
     double ms_upload, ms_tri, ms_lbvh, ms_delaunay, ms_cells, ms_aug, ms_proj, ms_k1, ms_grid, ms_total;
     /* Voronoi vertices per non-empty tau-cell of the augmentation: median and maximum */
     int64_t aug_cell_median, aug_cell_max;
+    /* cells clipped on the host although gpu_cells was set (beyond the device capacity) */
+    int64_t n_cells_host;
+    /* with gpu_cells: the device clip kernel (CUDA events) and the host clip of the rest */
+    double ms_cells_kernel, ms_cells_fallback;
 } p2m_stats;
 
 /* Per-call query counters (Section 4.1, Table 1 "Queried"). */
@@ -180,6 +187,13 @@ int p2m_query_signed(p2m_index* h, const float* d_pts, int64_t n, float* d_sdist
  * OOM, CUDA. */
 int p2m_mesh_distance(p2m_index* h, const float* d_verts_b, int64_t n_verts_b, const int32_t* d_tris_b,
                       int64_t n_tris_b, int subdivisions, double* h_out, void* stream);
+
+/* Both directions between the meshes of two single-mesh indexes, sampled as in
+ * p2m_mesh_distance: h_out[7] = (min, max, mean) of mesh B's samples against A, the same
+ * for A's samples against B, and the symmetric Hausdorff distance over the samples,
+ * max(h_out[1], h_out[4]).  Allocates its sample buffers; synchronises `stream`.  Errors:
+ * INVALID_ARG, OOM, CUDA. */
+int p2m_mesh_distance_pair(p2m_index* a, p2m_index* b, int subdivisions, double* h_out, void* stream);
 
 /* The same query from host memory: copies h_pts in chunks to the device, runs the query
  * and copies the results back.  Host
@@ -296,6 +310,14 @@ int p2m_query_noalloc(p2m_index* h, const float* d_pts, int64_t n, float* d_dist
  * Errors: INVALID_ARG (NULL, n < 4, a site outside D), INTERNAL. */
 int p2m_voronoi_cells(const float* h_sites, int64_t n, const double* dom_lo, const double* dom_hi, int seed,
                       float* h_sites_out, int64_t* h_corner_off, double* h_corners, int64_t* n_corners);
+
+/* The same cells clipped on the GPU (the path p2m_build takes with gpu_cells = 1): the same
+ * arguments and outputs, plus *n_host = the cells beyond the device clipper's capacity that
+ * were clipped on the host, and the stream the device work runs on.  Corners within 1e-12 of
+ * the domain diagonal are merged.  Errors: INVALID_ARG, OOM, CUDA, INTERNAL. */
+int p2m_voronoi_cells_device(const float* h_sites, int64_t n, const double* dom_lo, const double* dom_hi, int seed,
+                             float* h_sites_out, int64_t* h_corner_off, double* h_corners, int64_t* n_corners,
+                             int64_t* n_host, void* stream);
 
 #ifdef __cplusplus
 }

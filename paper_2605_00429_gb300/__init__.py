@@ -30,7 +30,7 @@ class BuildParams(ctypes.Structure):
                 ("density_factor", ctypes.c_float), ("density_min", ctypes.c_int), ("ring_sites", ctypes.c_int),
                 ("ring_radius_scale", ctypes.c_float), ("build_eps_rel", ctypes.c_float),
                 ("nn_grid_res", ctypes.c_int), ("schedule", ctypes.c_int), ("deterministic", ctypes.c_int),
-                ("seed", ctypes.c_int), ("long_list", ctypes.c_int)]
+                ("seed", ctypes.c_int), ("long_list", ctypes.c_int), ("gpu_cells", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -41,7 +41,8 @@ class Stats(ctypes.Structure):
         [("domain_lo", ctypes.c_double * 3), ("domain_hi", ctypes.c_double * 3), ("bbox_diag", ctypes.c_double)] + \
         [(n, ctypes.c_double) for n in ("ms_upload", "ms_tri", "ms_lbvh", "ms_delaunay", "ms_cells", "ms_aug",
                                         "ms_proj", "ms_k1", "ms_grid", "ms_total")] + \
-        [("aug_cell_median", ctypes.c_int64), ("aug_cell_max", ctypes.c_int64)]
+        [("aug_cell_median", ctypes.c_int64), ("aug_cell_max", ctypes.c_int64), ("n_cells_host", ctypes.c_int64),
+         ("ms_cells_kernel", ctypes.c_double), ("ms_cells_fallback", ctypes.c_double)]
 
     def as_dict(self):
         d = {}
@@ -83,9 +84,11 @@ SIGNATURES = {
     "p2m_get_lists": ([_P, _I, _P, _P], _I),
     "p2m_get_balls": ([_P, _I, _P, _P, _P], _I),
     "p2m_voronoi_cells": ([_P, _I64, _P, _P, _I, _P, _P, _P, _P], _I),
+    "p2m_voronoi_cells_device": ([_P, _I64, _P, _P, _I, _P, _P, _P, _P, _P, _P], _I),
     "p2m_query_noalloc": ([_P, _P, _I64, _P, _P, _P, _P, _P], _I),
     "p2m_query_signed": ([_P, _P, _I64, _P, _P, _P, _P, _P], _I),
     "p2m_mesh_distance": ([_P, _P, _I64, _P, _I64, _I, _P, _P], _I),
+    "p2m_mesh_distance_pair": ([_P, _P, _I, _P, _P], _I),
 }
 NOALLOC_MAX_QUERIES = 262144
 
@@ -230,6 +233,15 @@ class P2MIndex:
                                        out.ctypes.data_as(_P), _stream_ptr(stream)))
         return float(out[0]), float(out[1]), float(out[2])
 
+    def mesh_distance_pair(self, other, subdivisions=4, stream=None):
+        """Both directions between this index's mesh (A) and another single-mesh index's (B):
+        a dict with (min, max, mean) of B's samples against A ("b_to_a"), of A's against B
+        ("a_to_b") and the symmetric Hausdorff distance over the samples ("hausdorff")."""
+        out = np.zeros(7)
+        _check(lib().p2m_mesh_distance_pair(self._h, other._h, int(subdivisions), out.ctypes.data_as(_P),
+                                            _stream_ptr(stream)))
+        return {"b_to_a": tuple(out[0:3]), "a_to_b": tuple(out[3:6]), "hausdorff": float(out[6])}
+
     def query_host(self, pts: np.ndarray, h_dist=None, h_closest=None, h_tri=None, h_bary=None):
         """Host-memory query (copies inside the library).  Arrays may be pinned torch CPU
         tensors or numpy arrays; returns the output arrays."""
@@ -334,6 +346,26 @@ def voronoi_cells(sites, dom_lo, dom_hi, seed=1):
                                    moved.ctypes.data_as(_P), off.ctypes.data_as(_P), cor.ctypes.data_as(_P),
                                    ctypes.byref(cnt)))
     return moved, off, cor[:cnt.value]
+
+
+def voronoi_cells_device(sites, dom_lo, dom_hi, seed=1, stream=None):
+    """The same cells clipped on the GPU (the build's default path).  Returns (moved sites,
+    corner offsets, corners, number of cells that were clipped on the host instead)."""
+    s = np.ascontiguousarray(np.asarray(sites, dtype=np.float32).reshape(-1, 3))
+    lo = np.ascontiguousarray(np.asarray(dom_lo, dtype=np.float64))
+    hi = np.ascontiguousarray(np.asarray(dom_hi, dtype=np.float64))
+    n = s.shape[0]
+    cnt, n_host = ctypes.c_int64(), ctypes.c_int64()
+    args = (s.ctypes.data_as(_P), n, lo.ctypes.data_as(_P), hi.ctypes.data_as(_P), seed)
+    _check(lib().p2m_voronoi_cells_device(*args, None, None, None, ctypes.byref(cnt), ctypes.byref(n_host),
+                                          _stream_ptr(stream)))
+    moved = np.empty((n, 3), np.float32)
+    off = np.empty(n + 1, np.int64)
+    cor = np.empty((max(cnt.value, 1), 3), np.float64)
+    _check(lib().p2m_voronoi_cells_device(*args, moved.ctypes.data_as(_P), off.ctypes.data_as(_P),
+                                          cor.ctypes.data_as(_P), ctypes.byref(cnt), ctypes.byref(n_host),
+                                          _stream_ptr(stream)))
+    return moved, off, cor[:cnt.value], n_host.value
 
 
 def _make_function():

@@ -335,6 +335,7 @@ int p2m_default_params(p2m_build_params* out) {
     out->schedule = 0;
     out->deterministic = 1;
     out->seed = 1;
+    out->gpu_cells = 1;
     return P2M_OK;
 }
 

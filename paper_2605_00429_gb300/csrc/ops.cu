@@ -150,6 +150,19 @@ __global__ void k_dist_stats(const float* __restrict__ d, int64_t n, unsigned* _
 
 extern "C" {
 
+int p2m_mesh_distance_pair(p2m_index* a, p2m_index* b, int subdivisions, double* h_out, void* stream) {
+    if (!a || !b || a->meshes.size() != 1 || b->meshes.size() != 1 || !h_out)
+        return fail(P2M_ERR_INVALID_ARG, "p2m_mesh_distance_pair needs two single-mesh indexes and h_out");
+    const MeshData& ma = *a->meshes[0];
+    const MeshData& mb = *b->meshes[0];
+    P2M_TRY(p2m_mesh_distance(a, mb.d_verts.as<const float>(), mb.n_verts, mb.d_tris.as<const int32_t>(), mb.n_tris,
+                              subdivisions, h_out, stream));
+    P2M_TRY(p2m_mesh_distance(b, ma.d_verts.as<const float>(), ma.n_verts, ma.d_tris.as<const int32_t>(), ma.n_tris,
+                              subdivisions, h_out + 3, stream));
+    h_out[6] = std::max(h_out[1], h_out[4]);
+    return P2M_OK;
+}
+
 int p2m_mesh_distance(p2m_index* h, const float* d_verts_b, int64_t n_verts_b, const int32_t* d_tris_b,
                       int64_t n_tris_b, int subdivisions, double* h_out, void* stream) {
     if (!h || h->meshes.size() != 1) return fail(P2M_ERR_INVALID_ARG, "p2m_mesh_distance needs a single-mesh index");

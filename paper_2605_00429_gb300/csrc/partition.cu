@@ -265,9 +265,19 @@ int build_partition(MeshData& m, const p2m_build_params& prm, p2m_index* h, cuda
     st.ms_aug = t2 - t1;
     st.n_dense_cells = n_dense;
     st.n_delaunay_tets = ss.dt.count_real_tets();
-    ss.neighbour_csr();
-    if (ss.clip_cells(m.dom_lo, m.dom_hi, m.diag, hardware_threads()))
+    ss.neighbour_csr();  // the Delaunay adjacency, nearest first: counted with the triangulation
+    st.ms_delaunay += ms_now() - t2;
+    t2 = ms_now();
+    if (prm.gpu_cells) {
+        int64_t n_host = 0;
+        const int rc = ss.clip_cells_gpu(m.dom_lo, m.dom_hi, m.diag, hardware_threads(), s, &n_host,
+                                         &st.ms_cells_kernel, &st.ms_cells_fallback);
+        if (rc == -2) return fail(P2M_ERR_CUDA, "device cell clipping failed");
+        if (rc) return fail(P2M_ERR_INTERNAL, "a Voronoi cell clipped to nothing");
+        st.n_cells_host = n_host;
+    } else if (ss.clip_cells(m.dom_lo, m.dom_hi, m.diag, hardware_threads())) {
         return fail(P2M_ERR_INTERNAL, "a Voronoi cell clipped to nothing");
+    }
     double t3 = ms_now();
     st.ms_cells = t3 - t2;
     const int S = (int)ss.pts.size();
@@ -510,8 +520,9 @@ int build_partition(MeshData& m, const p2m_build_params& prm, p2m_index* h, cuda
 
 // ----------------------------------------------------------------------------- host-only API
 
-extern "C" int p2m_voronoi_cells(const float* h_sites, int64_t n, const double* dom_lo, const double* dom_hi, int seed,
-                                 float* h_sites_out, int64_t* h_corner_off, double* h_corners, int64_t* n_corners) {
+static int voronoi_cells(const float* h_sites, int64_t n, const double* dom_lo, const double* dom_hi, int seed,
+                         float* h_sites_out, int64_t* h_corner_off, double* h_corners, int64_t* n_corners,
+                         bool device, int64_t* n_host, void* stream) {
     using namespace p2m;
     if (!h_sites || n < 4 || !dom_lo || !dom_hi || !n_corners) return fail(P2M_ERR_INVALID_ARG, "bad arguments");
     SiteSet ss;
@@ -534,7 +545,13 @@ extern "C" int p2m_voronoi_cells(const float* h_sites, int64_t n, const double* 
     ss.neighbour_csr();
     double diag = 0;
     for (int k = 0; k < 3; ++k) diag += (dom_hi[k] - dom_lo[k]) * (dom_hi[k] - dom_lo[k]);
-    if (ss.clip_cells(dom_lo, dom_hi, std::sqrt(diag), hardware_threads())) return fail(P2M_ERR_INTERNAL, "empty cell");
+    if (device) {
+        const int rc = ss.clip_cells_gpu(dom_lo, dom_hi, std::sqrt(diag), hardware_threads(), stream, n_host);
+        if (rc == -2) return fail(P2M_ERR_CUDA, "device cell clipping failed");
+        if (rc) return fail(P2M_ERR_INTERNAL, "empty cell");
+    } else if (ss.clip_cells(dom_lo, dom_hi, std::sqrt(diag), hardware_threads())) {
+        return fail(P2M_ERR_INTERNAL, "empty cell");
+    }
     *n_corners = ss.cell_off[n];
     if (h_sites_out)
         for (int64_t i = 0; i < n; ++i) {
@@ -545,4 +562,17 @@ extern "C" int p2m_voronoi_cells(const float* h_sites, int64_t n, const double* 
     if (h_corner_off) std::memcpy(h_corner_off, ss.cell_off.data(), sizeof(int64_t) * (n + 1));
     if (h_corners) std::memcpy(h_corners, ss.cell_xyz.data(), sizeof(double) * ss.cell_xyz.size());
     return P2M_OK;
+}
+
+extern "C" int p2m_voronoi_cells(const float* h_sites, int64_t n, const double* dom_lo, const double* dom_hi, int seed,
+                                 float* h_sites_out, int64_t* h_corner_off, double* h_corners, int64_t* n_corners) {
+    return voronoi_cells(h_sites, n, dom_lo, dom_hi, seed, h_sites_out, h_corner_off, h_corners, n_corners, false,
+                         nullptr, nullptr);
+}
+
+extern "C" int p2m_voronoi_cells_device(const float* h_sites, int64_t n, const double* dom_lo, const double* dom_hi,
+                                        int seed, float* h_sites_out, int64_t* h_corner_off, double* h_corners,
+                                        int64_t* n_corners, int64_t* n_host, void* stream) {
+    return voronoi_cells(h_sites, n, dom_lo, dom_hi, seed, h_sites_out, h_corner_off, h_corners, n_corners, true,
+                         n_host, stream);
 }

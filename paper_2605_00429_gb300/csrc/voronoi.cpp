@@ -34,6 +34,8 @@ static inline uint64_t morton_key(const IPt& p, int64_t R) {
 
 void SiteSet::world(int i, double out[3]) const { lat.to_world(pts[i], out); }
 
+int hardware_threads();
+
 // Insert sites [first, pts.size()) into the triangulation in Morton order; a site whose
 // insertion fails (flat tetrahedron or exact duplicate) is moved by one lattice step.
 int SiteSet::triangulate_from(int first, uint64_t seed, std::string& err) {
@@ -84,63 +86,92 @@ void SiteSet::neighbour_csr() {
         nb_off[s + 1] = nb_off[s] + (int64_t)tmp[s].size();
         nb_id.insert(nb_id.end(), tmp[s].begin(), tmp[s].end());
     }
-}
-
-// Corners of every site's cell: D cut by the bisectors of its Delaunay neighbours,
-// nearest neighbour first.  Threads split the sites.
-int SiteSet::clip_cells(const double dom_lo[3], const double dom_hi[3], double diag, int n_threads) {
-    constexpr int kMaxClip = 256;
-    const int n = (int)pts.size();
-    cell_off.assign(n + 1, 0);
-    std::vector<std::vector<double>> corners(n);
-    std::atomic<int> next(0), bad(0);
-    const double tol = 1e-12 * diag;
+    // each site's neighbours nearest first (squared distance, then id): the order both cell
+    // clippers cut in
+    std::atomic<int> next(0);
     auto work = [&]() {
-        Clipper C;
         std::vector<std::pair<double, int>> order;
         while (true) {
             const int s = next.fetch_add(1);
             if (s >= n) break;
             double ps[3];
             world(s, ps);
-            C.box(dom_lo, dom_hi);
             order.clear();
             for (int64_t k = nb_off[s]; k < nb_off[s + 1]; ++k) {
                 double pt[3];
                 world(nb_id[k], pt);
-                const double d2 = (pt[0] - ps[0]) * (pt[0] - ps[0]) + (pt[1] - ps[1]) * (pt[1] - ps[1]) +
-                                  (pt[2] - ps[2]) * (pt[2] - ps[2]);
-                order.push_back({d2, nb_id[k]});
+                const double dx = pt[0] - ps[0], dy = pt[1] - ps[1], dz = pt[2] - ps[2];
+                order.push_back({dx * dx + dy * dy + dz * dz, nb_id[k]});
             }
             std::sort(order.begin(), order.end());
-            int used = 0;
-            for (auto& o : order) {
-                // Nearest first: a neighbour t can cut the cell only if its bisector, at
-                // distance |s - t| / 2 from s, comes within the cell's radius about s.  After
-                // kMaxClip neighbours the clip stops; the cell is then a superset of the true
-                // one, which is still a valid region for Eq. 3.
-                if (0.25 * o.first > C.radius2_from(ps) * (1.0 + 1e-9) + tol * tol) break;
-                if (++used > kMaxClip) break;
-                double pt[3];
-                world(o.second, pt);
-                double nrm[3] = {pt[0] - ps[0], pt[1] - ps[1], pt[2] - ps[2]};
-                const double len = std::sqrt(nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2]);
-                if (!(len > 0)) continue;
-                for (double& c : nrm) c /= len;
-                const double d = 0.5 * (nrm[0] * (pt[0] + ps[0]) + nrm[1] * (pt[1] + ps[1]) + nrm[2] * (pt[2] + ps[2]));
-                if (!C.clip(nrm, d, tol)) { bad.fetch_add(1); break; }
+            for (size_t k = 0; k < order.size(); ++k) nb_id[nb_off[s] + (int64_t)k] = order[k].second;
+        }
+    };
+    std::vector<std::thread> th;
+    for (int t = 0; t < std::max(1, std::min(hardware_threads(), n)); ++t) th.emplace_back(work);
+    for (auto& t : th) t.join();
+}
+
+// Corners of site s's cell: D cut by the bisectors of its Delaunay neighbours, nearest
+// neighbour first (the neighbour lists are kept in that order).  A neighbour t can cut the
+// cell only if its bisector, at distance |s - t| / 2 from s, comes within the cell's radius
+// about s; after kMaxClip neighbours the clip stops, and the cell is then a superset of the
+// true one, which is still a valid region for Eq. 3.  Returns false if the cell clipped to
+// nothing.
+bool SiteSet::clip_one(int s, const double dom_lo[3], const double dom_hi[3], double tol, Clipper& C) const {
+    double ps[3];
+    world(s, ps);
+    C.box(dom_lo, dom_hi);
+    int used = 0;
+    for (int64_t k = nb_off[s]; k < nb_off[s + 1]; ++k) {
+        double pt[3];
+        world(nb_id[k], pt);
+        double nrm[3] = {pt[0] - ps[0], pt[1] - ps[1], pt[2] - ps[2]};
+        const double d2 = nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2];
+        if (0.25 * d2 > C.radius2_from(ps) * (1.0 + 1e-9) + tol * tol) break;
+        if (++used > kMaxClip) break;
+        const double len = std::sqrt(d2);
+        if (!(len > 0)) continue;
+        for (double& c : nrm) c /= len;
+        const double d = 0.5 * (nrm[0] * (pt[0] + ps[0]) + nrm[1] * (pt[1] + ps[1]) + nrm[2] * (pt[2] + ps[2]));
+        if (!C.clip(nrm, d, tol)) return false;
+    }
+    return true;
+}
+
+// The cells of all sites (or of the listed ones: `only`), threads splitting the sites.
+int SiteSet::clip_cells(const double dom_lo[3], const double dom_hi[3], double diag, int n_threads) {
+    const int n = (int)pts.size();
+    std::vector<std::vector<double>> corners(n);
+    if (clip_some(nullptr, n, dom_lo, dom_hi, diag, n_threads, corners)) return -1;
+    cell_off.assign(n + 1, 0);
+    for (int s = 0; s < n; ++s) cell_off[s + 1] = cell_off[s] + (int64_t)(corners[s].size() / 3);
+    cell_xyz.resize(cell_off[n] * 3);
+    for (int s = 0; s < n; ++s) std::copy(corners[s].begin(), corners[s].end(), cell_xyz.begin() + cell_off[s] * 3);
+    return 0;
+}
+
+int SiteSet::clip_some(const int* only, int count, const double dom_lo[3], const double dom_hi[3], double diag,
+                       int n_threads, std::vector<std::vector<double>>& corners) const {
+    std::atomic<int> next(0), bad(0);
+    const double tol = clip_tol(diag);
+    auto work = [&]() {
+        Clipper C;
+        while (true) {
+            const int k = next.fetch_add(1);
+            if (k >= count) break;
+            const int s = only ? only[k] : k;
+            if (!clip_one(s, dom_lo, dom_hi, tol, C)) {
+                bad.fetch_add(1);
+                continue;
             }
             corners[s] = C.V;
         }
     };
     std::vector<std::thread> th;
-    for (int t = 0; t < std::max(1, n_threads); ++t) th.emplace_back(work);
+    for (int t = 0; t < std::max(1, std::min(n_threads, count)); ++t) th.emplace_back(work);
     for (auto& t : th) t.join();
-    if (bad.load()) return -1;
-    for (int s = 0; s < n; ++s) cell_off[s + 1] = cell_off[s] + (int64_t)(corners[s].size() / 3);
-    cell_xyz.resize(cell_off[n] * 3);
-    for (int s = 0; s < n; ++s) std::copy(corners[s].begin(), corners[s].end(), cell_xyz.begin() + cell_off[s] * 3);
-    return 0;
+    return bad.load() ? -1 : 0;
 }
 
 int hardware_threads() {

@@ -33,3 +33,20 @@ def test_mesh_distance_vs_oracle(k):
     ref = oracle.closest(a.verts, a.tris, _samples(b, k).astype(np.float32))["dist"]
     tol = 2e-6 * a.diag()
     assert abs(mn - ref.min()) <= tol and abs(mx - ref.max()) <= tol and abs(mean - ref.mean()) <= tol
+
+
+def test_mesh_distance_pair_vs_oracle():
+    """Both directions and the symmetric Hausdorff distance over the samples."""
+    import paper_2605_00429_gb300 as p2m
+    a = W.displace_radial(W.icosphere(3), 0.05, 1)
+    b = W.capped_cylinder(24, 6)
+    b.verts[:] = b.verts * np.float32(0.4) + np.float32(0.3)
+    ia, ib = p2m.P2MIndex(a.verts, a.tris), p2m.P2MIndex(b.verts, b.tris)
+    k = 2
+    r = ia.mesh_distance_pair(ib, k)
+    d_ba = oracle.closest(a.verts, a.tris, _samples(b, k).astype(np.float32))["dist"]
+    d_ab = oracle.closest(b.verts, b.tris, _samples(a, k).astype(np.float32))["dist"]
+    tol = 2e-6 * max(a.diag(), b.diag())
+    for got, ref in ((r["b_to_a"], d_ba), (r["a_to_b"], d_ab)):
+        assert abs(got[0] - ref.min()) <= tol and abs(got[1] - ref.max()) <= tol and abs(got[2] - ref.mean()) <= tol
+    assert abs(r["hausdorff"] - max(d_ba.max(), d_ab.max())) <= tol
