@@ -21,6 +21,9 @@
 #include <chrono>
 #include <cstring>
 
+#include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_run_length_encode.cuh>
+
 #include "host_geom.h"
 #include "p2m_internal.h"
 #include "voronoi.h"
@@ -314,6 +317,76 @@ int SiteSet::clip_cells_gpu(const double dom_lo[3], const double dom_hi[3], doub
         if (state[i] != CELL_OK && !hc[i].empty())
             std::memcpy(&cell_xyz[3 * (size_t)cell_off[i]], hc[i].data(), sizeof(double) * hc[i].size());
     if (n_host) *n_host = (int64_t)(n_early + late.size());
+    return 0;
+}
+
+// The augmentation's binning (Section 3.2) on the device: each Voronoi vertex inside D (world
+// coordinates w[n][3]) falls into tau-cell (floor((w - lo) / tau)) with key (cz * ncy + cy) *
+// ncx + cx; vertices outside D get the key ncx * ncy * ncz and sort last.  A radix sort and a
+// run-length encoding give the occupied cells' keys (ascending) and their vertex counts.
+__global__ void k_bin_keys(const double* __restrict__ w, int64_t n, double3 lo, double3 hi, double tau, int64_t ncx,
+                           int64_t ncy, unsigned long long top, unsigned long long* __restrict__ key) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const double x = w[3 * i], y = w[3 * i + 1], z = w[3 * i + 2];
+        const bool in = x >= lo.x && x <= hi.x && y >= lo.y && y <= hi.y && z >= lo.z && z <= hi.z;
+        unsigned long long k = top;
+        if (in) {
+            const int64_t cx = (int64_t)floor((x - lo.x) / tau), cy = (int64_t)floor((y - lo.y) / tau),
+                          cz = (int64_t)floor((z - lo.z) / tau);
+            k = (unsigned long long)((cz * ncy + cy) * ncx + cx);
+        }
+        key[i] = k;
+    }
+}
+
+int bin_points_gpu(const std::vector<double>& w, const double lo[3], const double hi[3], double tau,
+                   const int64_t ncell[3], std::vector<uint64_t>& keys, std::vector<int>& counts, void* stream) {
+    cudaStream_t s = (cudaStream_t)stream;
+    keys.clear();
+    counts.clear();
+    const int64_t n = (int64_t)(w.size() / 3);
+    if (n == 0) return 0;
+    if (n > 0x7fffffffLL) return -1;
+    // every key of a cell inside D is below ncx * ncy * ncz (each coordinate stays below its
+    // axis count: the counts carry two cells of margin over the extent / tau)
+    const unsigned long long top = (unsigned long long)(ncell[0] * ncell[1] * ncell[2]);
+    int bits = 1;
+    while (bits < 64 && (top >> bits) != 0) ++bits;
+    DevBuf d_w, d_k0, d_k1, d_uniq, d_cnt, d_runs, d_tmp;
+    size_t t_sort = 0, t_rle = 0;
+    if (cub::DeviceRadixSort::SortKeys(nullptr, t_sort, (unsigned long long*)nullptr, (unsigned long long*)nullptr,
+                                       (int)n, 0, bits, s) ||
+        cub::DeviceRunLengthEncode::Encode(nullptr, t_rle, (unsigned long long*)nullptr, (unsigned long long*)nullptr,
+                                           (int*)nullptr, (int*)nullptr, (int)n, s))
+        return -1;
+    if (d_w.alloc(sizeof(double) * w.size()) || d_k0.alloc(sizeof(unsigned long long) * n) ||
+        d_k1.alloc(sizeof(unsigned long long) * n) || d_uniq.alloc(sizeof(unsigned long long) * n) ||
+        d_cnt.alloc(sizeof(int) * n) || d_runs.alloc(sizeof(int)) || d_tmp.alloc(std::max(t_sort, t_rle) + 16))
+        return -1;
+    if (cudaMemcpyAsync(d_w.p, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice, s)) return -1;
+    k_bin_keys<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, s>>>(
+        d_w.as<double>(), n, make_double3(lo[0], lo[1], lo[2]), make_double3(hi[0], hi[1], hi[2]), tau, ncell[0],
+        ncell[1], top, d_k0.as<unsigned long long>());
+    if (cudaGetLastError() != cudaSuccess) return -1;
+    cub::DoubleBuffer<unsigned long long> db(d_k0.as<unsigned long long>(), d_k1.as<unsigned long long>());
+    if (cub::DeviceRadixSort::SortKeys(d_tmp.p, t_sort, db, (int)n, 0, bits, s) ||
+        cub::DeviceRunLengthEncode::Encode(d_tmp.p, t_rle, db.Current(), d_uniq.as<unsigned long long>(),
+                                           d_cnt.as<int>(), d_runs.as<int>(), (int)n, s))
+        return -1;
+    int runs = 0;
+    if (cudaMemcpyAsync(&runs, d_runs.p, sizeof(int), cudaMemcpyDeviceToHost, s) || cudaStreamSynchronize(s)) return -1;
+    std::vector<unsigned long long> u(runs);
+    counts.resize(runs);
+    if (runs > 0 &&
+        (cudaMemcpyAsync(u.data(), d_uniq.p, sizeof(unsigned long long) * runs, cudaMemcpyDeviceToHost, s) ||
+         cudaMemcpyAsync(counts.data(), d_cnt.p, sizeof(int) * runs, cudaMemcpyDeviceToHost, s) ||
+         cudaStreamSynchronize(s)))
+        return -1;
+    if (runs > 0 && u.back() == top) {  // the vertices outside D
+        u.pop_back();
+        counts.pop_back();
+    }
+    keys.assign(u.begin(), u.end());
     return 0;
 }
 

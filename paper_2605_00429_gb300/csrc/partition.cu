@@ -116,7 +116,7 @@ struct PointHash {
 // site plus a ring of auxiliary sites on an enclosing sphere for each; ring sites that fall
 // near an existing site or inside another flagged cell's bounding sphere are dropped.
 // Returns the number of auxiliary sites appended to ss.pts.
-static int augment(SiteSet& ss, MeshData& m, const p2m_build_params& prm, int64_t& n_dense) {
+static int augment(SiteSet& ss, MeshData& m, const p2m_build_params& prm, int64_t& n_dense, cudaStream_t s) {
     n_dense = 0;
     // tau from the mean edge length
     double sum = 0;
@@ -131,37 +131,49 @@ static int augment(SiteSet& ss, MeshData& m, const p2m_build_params& prm, int64_
         }
     const double tau = prm.tau_scale * sum / std::max<int64_t>(ne, 1);
     if (!(tau > 0)) return 0;
+    // the Voronoi vertices (circumcentres of the Delaunay tetrahedra) in world coordinates
     std::vector<double> cc;
     ss.dt.circumcentres(cc);
-    std::unordered_map<uint64_t, int> count;
-    auto cell_of = [&](const double* x, int64_t* c) {
-        for (int k = 0; k < 3; ++k) c[k] = (int64_t)std::floor((x[k] - m.dom_lo[k]) / tau);
-    };
-    const int64_t nc = (int64_t)std::ceil((m.dom_hi[0] - m.dom_lo[0]) / tau) + 2;
-    auto key = [&](const int64_t* c) { return (uint64_t)((c[2] * nc + c[1]) * nc + c[0]); };
-    for (size_t i = 0; i + 2 < cc.size(); i += 3) {
-        double w[3];
-        for (int k = 0; k < 3; ++k) w[k] = (cc[i + k] + (double)ss.lat.c[k]) * ss.lat.h;
-        bool in = true;
-        for (int k = 0; k < 3; ++k) in &= w[k] >= m.dom_lo[k] && w[k] <= m.dom_hi[k];
-        if (!in) continue;
-        int64_t c[3];
-        cell_of(w, c);
-        count[key(c)]++;
+    for (size_t i = 0; i + 2 < cc.size(); i += 3)
+        for (int k = 0; k < 3; ++k) cc[i + k] = (cc[i + k] + (double)ss.lat.c[k]) * ss.lat.h;
+    // tau-cells per axis; a cell's key is (cz * ncy + cy) * ncx + cx
+    int64_t ncell[3];
+    for (int k = 0; k < 3; ++k) ncell[k] = (int64_t)std::ceil((m.dom_hi[k] - m.dom_lo[k]) / tau) + 2;
+    const int64_t ncx = ncell[0], ncy = ncell[1];
+    // occupied tau-cells and their vertex counts: binned on the device, or on the host
+    std::vector<uint64_t> cell_key;
+    std::vector<int> cell_count;
+    if (prm.gpu_cells) {
+        if (bin_points_gpu(cc, m.dom_lo, m.dom_hi, tau, ncell, cell_key, cell_count, s))
+            return fail(P2M_ERR_CUDA, "device binning of the Voronoi vertices failed");
+    } else {
+        std::unordered_map<uint64_t, int> count;
+        for (size_t i = 0; i + 2 < cc.size(); i += 3) {
+            const double* w = &cc[i];
+            bool in = true;
+            for (int k = 0; k < 3; ++k) in &= w[k] >= m.dom_lo[k] && w[k] <= m.dom_hi[k];
+            if (!in) continue;
+            int64_t c[3];
+            for (int k = 0; k < 3; ++k) c[k] = (int64_t)std::floor((w[k] - m.dom_lo[k]) / tau);
+            count[(uint64_t)((c[2] * ncy + c[1]) * ncx + c[0])]++;
+        }
+        for (auto& kv : count) {
+            cell_key.push_back(kv.first);
+            cell_count.push_back(kv.second);
+        }
     }
-    if (count.empty()) return 0;
-    std::vector<int> vals;
-    for (auto& kv : count) vals.push_back(kv.second);
+    if (cell_key.empty()) return 0;
+    std::vector<int> vals(cell_count);
     std::nth_element(vals.begin(), vals.begin() + vals.size() / 2, vals.end());
     const double median = vals[vals.size() / 2];
     m.stats.aug_cell_median = (int64_t)median;
     m.stats.aug_cell_max = *std::max_element(vals.begin(), vals.end());
     const double thresh = std::max((double)prm.density_min, prm.density_factor * median);
     std::vector<std::array<double, 3>> centres;
-    for (auto& kv : count) {
-        if (kv.second <= thresh) continue;
-        const uint64_t k = kv.first;
-        const int64_t cx = (int64_t)(k % nc), cy = (int64_t)((k / nc) % nc), cz = (int64_t)(k / ((uint64_t)nc * nc));
+    for (size_t j = 0; j < cell_key.size(); ++j) {
+        if (cell_count[j] <= thresh) continue;
+        const uint64_t k = cell_key[j];
+        const int64_t cx = (int64_t)(k % ncx), cy = (int64_t)((k / ncx) % ncy), cz = (int64_t)(k / ((uint64_t)ncx * ncy));
         centres.push_back({m.dom_lo[0] + (cx + 0.5) * tau, m.dom_lo[1] + (cy + 0.5) * tau, m.dom_lo[2] + (cz + 0.5) * tau});
     }
     std::sort(centres.begin(), centres.end());
@@ -251,7 +263,8 @@ int build_partition(MeshData& m, const p2m_build_params& prm, p2m_index* h, cuda
     int n_aux = 0;
     int64_t n_dense = 0;
     if (prm.enable_aux) {
-        n_aux = augment(ss, m, prm, n_dense);
+        n_aux = augment(ss, m, prm, n_dense, s);
+        if (n_aux < 0) return n_aux;
         if (n_aux > 0) {
             // triangulate all sites again in one Morton order: inserting the auxiliary sites
             // into the finished triangulation would open very large cavities around the

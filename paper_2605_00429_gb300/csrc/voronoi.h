@@ -39,4 +39,10 @@ struct SiteSet {
 
 int hardware_threads();
 
+// Voronoi vertices w[n][3] inside [lo, hi] binned into tau-cells on the device (ncell[3]
+// cells per axis): the occupied cells' keys (cz * ncy + cy) * ncx + cx, ascending, and their
+// counts.  Returns 0, or -1 on a CUDA or allocation failure.
+int bin_points_gpu(const std::vector<double>& w, const double lo[3], const double hi[3], double tau,
+                   const int64_t ncell[3], std::vector<uint64_t>& keys, std::vector<int>& counts, void* stream);
+
 }  // namespace p2m

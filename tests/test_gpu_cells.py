@@ -76,4 +76,19 @@ def test_index_with_device_cells(p2m, mesh_name):
     np.testing.assert_array_equal(ra[2].cpu().numpy(), rb[2].cpu().numpy())
     sa, sb = a.stats(), b.stats()
     assert sb["n_cells_host"] == 0
-    assert sa["n_sites"] == sb["n_sites"]
+    # the augmentation's binning (device with gpu_cells=1, host otherwise) flags the same cells
+    for k in ("n_sites", "n_aux_sites", "n_dense_cells", "aug_cell_median", "aug_cell_max", "n_delaunay_tets"):
+        assert sa[k] == sb[k], k
+    if mesh_name == "cylinder_cone":
+        assert sa["n_aux_sites"] > 0
+
+
+def test_augmentation_binning_elongated_domain(p2m):
+    """Full-size cylinder + cone: its domain is 1.75x longer in z than in x, so the tau-grid
+    needs a cell count per axis.  Device and host binning must flag the same cells."""
+    mesh = W.cylinder_cone(512, 128, 64, 8)
+    sa = p2m.P2MIndex(mesh.verts, mesh.tris, gpu_cells=1).stats()
+    sb = p2m.P2MIndex(mesh.verts, mesh.tris, gpu_cells=0).stats()
+    assert sa["n_dense_cells"] > 0
+    for k in ("n_sites", "n_aux_sites", "n_dense_cells", "aug_cell_median", "aug_cell_max", "n_delaunay_tets"):
+        assert sa[k] == sb[k], k
