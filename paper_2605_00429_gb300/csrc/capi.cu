@@ -78,8 +78,7 @@ MeshView MeshData::view() const {
     v.sites = d_sites.as<const float4>();
     v.refs = d_refs.as<const float4>();
     v.row_off = d_row_off.as<const int32_t>();
-    v.row_tri = d_row_tri.as<const int32_t>();
-    v.row_key = d_row_key.as<const float>();
+    v.row_ent = d_row_ent.as<const int2>();
     v.chunk_off = d_chunk_off.as<const int32_t>();
     v.cbox = d_cbox.as<const float4>();
     v.l1_off = d_l1_off.as<const int32_t>();
@@ -481,8 +480,9 @@ int p2m_get_lists(const p2m_index* h, int mesh, int64_t* h_offsets, int32_t* h_t
     if (h_offsets)
         for (int64_t i = 0; i <= S; ++i) h_offsets[i] = off[i];
     if (h_tri_ids && m->nnz > 0) {
-        P2M_CUDA_TRY(cudaMemcpy(h_tri_ids, m->d_row_tri.p, sizeof(int32_t) * m->nnz, cudaMemcpyDeviceToHost));
-        for (int64_t k = 0; k < m->nnz; ++k) h_tri_ids[k] = m->orig[h_tri_ids[k]];  // caller's triangle ids
+        std::vector<int2> ent(m->nnz);
+        P2M_CUDA_TRY(cudaMemcpy(ent.data(), m->d_row_ent.p, sizeof(int2) * m->nnz, cudaMemcpyDeviceToHost));
+        for (int64_t k = 0; k < m->nnz; ++k) h_tri_ids[k] = m->orig[ent[k].x];  // caller's triangle ids
     }
     return P2M_OK;
 }

@@ -273,6 +273,13 @@ __global__ void k_i64_to_i32(const int64_t* __restrict__ a, int32_t* __restrict_
 }
 
 // Builds m.d_row_off / m.d_row_tri from the device ball table (d_balls, d_ball_off).
+// List entries as (triangle, key bits) pairs: the thread scan reads both with one 8-byte load.
+__global__ void k_pack_entries(const int32_t* __restrict__ row_tri, const float* __restrict__ row_key, int64_t nnz,
+                               int2* __restrict__ row_ent) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < nnz; j += (int64_t)gridDim.x * blockDim.x)
+        row_ent[j] = make_int2(row_tri[j], __float_as_int(row_key[j]));
+}
+
 int build_lists(MeshData& m, const float4* d_balls, const int64_t* d_ball_off, int n_sites, unsigned* status,
                 cudaStream_t s) {
     DevBuf cnt, off64, tmp;
@@ -375,6 +382,16 @@ int build_lists(MeshData& m, const float4* d_balls, const int64_t* d_ball_off, i
             m.d_chunk_off.as<int32_t>(), m.d_l1_off.as<int32_t>(), n_sites, m.d_cbox.as<float4>(), m.d_l1box.as<float4>());
         P2M_CUDA_TRY(cudaGetLastError());
     }
+    // the entries as (triangle, key) pairs; the separate arrays are released
+    P2M_TRY(m.d_row_ent.alloc(sizeof(int2) * std::max<int64_t>(nnz, 1)));
+    if (nnz > 0) {
+        k_pack_entries<<<(int)std::min<int64_t>((nnz + 255) / 256, 152 * 32), 256, 0, s>>>(
+            m.d_row_tri.as<int32_t>(), m.d_row_key.as<float>(), nnz, m.d_row_ent.as<int2>());
+        P2M_CUDA_TRY(cudaGetLastError());
+    }
+    P2M_CUDA_TRY(cudaStreamSynchronize(s));
+    m.d_row_tri.release();
+    m.d_row_key.release();
     // row statistics (Table 1 Max / Avg)
     std::vector<int64_t> c(n_sites);
     P2M_CUDA_TRY(cudaMemcpyAsync(c.data(), cnt.p, sizeof(int64_t) * n_sites, cudaMemcpyDeviceToHost, s));

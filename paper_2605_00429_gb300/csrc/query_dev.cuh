@@ -106,12 +106,13 @@ __device__ __forceinline__ unsigned long long scan_list(const MeshView& m, float
         if (!chunk_may_hit(m, c, q, bound)) continue;
         const int j0 = r0 + (c - c0) * kChunk, j1 = min(j0 + kChunk, r1);
         for (int j = j0; j < j1; ++j) {
-            if (sorted_list && __ldg(m.row_key + j) > bound + dq_up) {
+            const int2 e = __ldg(m.row_ent + j);
+            if (sorted_list && __int_as_float(e.y) > bound + dq_up) {
                 done = true;
                 break;
             }
             if (COUNT) ++n_entries;
-            const int f = __ldg(m.row_tri + j);
+            const int f = e.x;
             const float4 sp = __ldg(m.tsph + f);
             const float dx = q.x - sp.x, dy = q.y - sp.y, dz = q.z - sp.z;
             const float lim = bound + sp.w;
@@ -208,7 +209,7 @@ __device__ __forceinline__ bool warp_scan_list(const MeshView& m, float3 q, int 
         float s = 0.0f, t = 0.0f;
         if (j < min(r0 + (c + 1) * kChunk, r1)) {
             if (COUNT) ++n_entries;
-            const int f = __ldg(m.row_tri + j);
+            const int f = __ldg(&m.row_ent[j].x);
             const float4 sp = __ldg(m.tsph + f);
             const float dx = q.x - sp.x, dy = q.y - sp.y, dz = q.z - sp.z;
             const float lim = bound + sp.w;
