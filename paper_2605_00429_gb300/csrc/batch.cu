@@ -35,7 +35,7 @@ struct BatchArgs {
     float4* rec;        // sorted order: 32-byte result records, split after the warp pass
 };
 
-__global__ void __launch_bounds__(256) k_batch_thread(BatchArgs a) {
+__global__ void __launch_bounds__(256, 6) k_batch_thread(BatchArgs a) {
     __shared__ int s_tile;
     while (true) {
         if (threadIdx.x == 0) s_tile = atomicAdd(a.ctr, 1);

@@ -437,6 +437,9 @@ int p2m_get_stats(const p2m_index* h, p2m_stats* out) {
         a.ms_upload += b.ms_upload; a.ms_tri += b.ms_tri; a.ms_lbvh += b.ms_lbvh; a.ms_delaunay += b.ms_delaunay;
         a.ms_cells += b.ms_cells; a.ms_aug += b.ms_aug; a.ms_proj += b.ms_proj; a.ms_k1 += b.ms_k1;
         a.ms_grid += b.ms_grid; a.ms_total += b.ms_total;
+        a.n_cells_host += b.n_cells_host; a.ms_cells_kernel += b.ms_cells_kernel;
+        a.ms_cells_fallback += b.ms_cells_fallback;
+        a.aug_cell_max = std::max(a.aug_cell_max, b.aug_cell_max);
         rows += (double)b.n_sites;
     }
     a.avg_row = rows > 0 ? (double)a.nnz / rows : 0.0;

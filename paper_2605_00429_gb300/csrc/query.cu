@@ -20,7 +20,7 @@ namespace p2m {
 // Thread-per-query schedule: fused nearest-site search and list scan.  A query whose list
 // is longer than m.long_row is queued (query, site) for the warp-per-query scan.
 template <bool COUNT>
-__global__ void __launch_bounds__(256) k_query_thread(MeshView m, const float* __restrict__ pts, int64_t n,
+__global__ void __launch_bounds__(256, 6) k_query_thread(MeshView m, const float* __restrict__ pts, int64_t n,
                                                      float* __restrict__ dist, float* __restrict__ closest,
                                                      int32_t* __restrict__ tri_out, float* __restrict__ bary,
                                                      int32_t* __restrict__ rest, int* __restrict__ n_rest,
