@@ -90,6 +90,10 @@ typedef struct {
     /* Clip the Voronoi cells on the GPU in FP64 [1]; cells beyond the device clipper's fixed
      * capacity (58 cutting planes) are clipped on the host.  0 = every cell on the host. */
     int gpu_cells;
+    /* Chunks of the host-buffer query pipeline (p2m_query_host); 0 picks the default (2) [0].
+     * More chunks overlap copies and compute better; fewer keep more queries per grid cell
+     * in each chunk's Morton order. */
+    int pipe_chunks;
 } p2m_build_params;
 
 /* Build statistics (Section 4.1, Table 1: Max / Avg list length) and stage timings. */

@@ -30,7 +30,8 @@ class BuildParams(ctypes.Structure):
                 ("density_factor", ctypes.c_float), ("density_min", ctypes.c_int), ("ring_sites", ctypes.c_int),
                 ("ring_radius_scale", ctypes.c_float), ("build_eps_rel", ctypes.c_float),
                 ("nn_grid_res", ctypes.c_int), ("schedule", ctypes.c_int), ("deterministic", ctypes.c_int),
-                ("seed", ctypes.c_int), ("long_list", ctypes.c_int), ("gpu_cells", ctypes.c_int)]
+                ("seed", ctypes.c_int), ("long_list", ctypes.c_int), ("gpu_cells", ctypes.c_int),
+                ("pipe_chunks", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

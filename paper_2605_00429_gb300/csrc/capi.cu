@@ -143,6 +143,7 @@ static int validate_params(const p2m_build_params& p) {
     if (p.nn_grid_res < 0 || p.nn_grid_res > 1024) return fail(P2M_ERR_INVALID_ARG, "nn_grid_res out of range");
     if (p.schedule < 0 || p.schedule > 4) return fail(P2M_ERR_INVALID_ARG, "schedule must be 0..4");
     if (p.long_list < 0) return fail(P2M_ERR_INVALID_ARG, "long_list must be >= 0");
+    if (p.pipe_chunks < 0) return fail(P2M_ERR_INVALID_ARG, "pipe_chunks must be >= 0");
     return P2M_OK;
 }
 
