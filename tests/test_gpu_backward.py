@@ -92,10 +92,13 @@ def test_autograd_function(p2m):
     assert verts.grad is not None and torch.isfinite(verts.grad).all()
 
 
-def test_query_host_matches_device(p2m):
+@pytest.mark.parametrize("n_queries,chunks", [(300_000, 0), (2_500_000, 3)])
+def test_query_host_matches_device(p2m, n_queries, chunks):
+    """The host-buffer pipeline (one chunk, or three 1M-point chunks on three streams) gives
+    the device query's answers bit for bit."""
     import torch
-    mesh, q = W.workload_large(300_000, k=4)
-    idx = p2m.P2MIndex(mesh.verts, mesh.tris)
+    mesh, q = W.workload_large(n_queries, k=4)
+    idx = p2m.P2MIndex(mesh.verts, mesh.tris, pipe_chunks=chunks)
     d, c, t, b = idx.query(torch.from_numpy(q).cuda())
     hd = np.empty(len(q), np.float32)
     hc = np.empty((len(q), 3), np.float32)
