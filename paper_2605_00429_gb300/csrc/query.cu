@@ -10,6 +10,7 @@
 //   K5  points outside the domain box D (or, defensively, whose list gave no triangle) are
 //       compacted and answered by the exact BVH search.
 #include <cub/device/device_radix_sort.cuh>
+#include <cub/device/device_scan.cuh>
 #include <cub/device/device_select.cuh>
 
 #include "host.h"
@@ -222,16 +223,31 @@ __device__ __forceinline__ unsigned spread8(unsigned v) {
     return v;
 }
 
-__global__ void k_query_keys(MeshView m, const float* __restrict__ pts, int64_t n, unsigned* __restrict__ key,
-                             int32_t* __restrict__ idx) {
+
+// Counting sort of the queries by the Morton code of their grid cell (mbits bits per axis,
+// G <= 2^mbits): each query takes its rank inside its cell from an atomic counter, an
+// exclusive scan of the counters gives each cell's first slot, and the points go straight to
+// their slots as (xyz, index).  Points outside the domain box get the last key and go last.
+// The order inside a cell is arbitrary; no result depends on it.
+__global__ void k_cell_rank(MeshView m, const float* __restrict__ pts, int64_t n, unsigned outside_key,
+                            unsigned* __restrict__ key, int32_t* __restrict__ rank, int* __restrict__ count) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float3 q = make_float3(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]);
         const float fx = (q.x - m.lo.x) * m.inv_h.x, fy = (q.y - m.lo.y) * m.inv_h.y, fz = (q.z - m.lo.z) * m.inv_h.z;
-        unsigned k = 0xffffffu;
+        unsigned k = outside_key;
         if (fx >= 0.0f && fy >= 0.0f && fz >= 0.0f && fx < (float)m.G && fy < (float)m.G && fz < (float)m.G)
             k = (spread8((unsigned)fx) << 2) | (spread8((unsigned)fy) << 1) | spread8((unsigned)fz);
         key[i] = k;
-        idx[i] = (int32_t)i;
+        rank[i] = atomicAdd(count + k, 1);
+    }
+}
+
+__global__ void k_cell_scatter(const float* __restrict__ pts, int64_t n, const unsigned* __restrict__ key,
+                               const int32_t* __restrict__ rank, const int* __restrict__ first,
+                               float4* __restrict__ qs) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t slot = (int64_t)__ldg(first + __ldg(key + i)) + __ldg(rank + i);
+        qs[slot] = make_float4(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2], __int_as_float((int)i));
     }
 }
 
@@ -273,9 +289,17 @@ int run_query(p2m_index* h, MeshData& m, const float* d_pts, int64_t n, float* d
         P2M_CUDA_TRY(cub::DeviceSelect::Flagged(nullptr, sel_tmp, (int2*)nullptr, (unsigned char*)nullptr, (int2*)nullptr,
                                                 (int*)nullptr, (int)n, s));
     }
-    const size_t a4 = up(sizeof(int32_t) * n), tmp_bytes = up(std::max(sort_tmp, sel_tmp));
+    // counting sort over the Morton codes of the grid cells: mbits bits per axis
+    int mbits = 1;
+    while ((1 << mbits) < v.G) ++mbits;
+    const int64_t n_keys = (int64_t)1 << (3 * mbits);  // key n_keys: outside the domain box
+    size_t scan_tmp = 0;
+    if (sorted)
+        P2M_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, scan_tmp, (int*)nullptr, (int*)nullptr, (int)(n_keys + 1), s));
+    const size_t a4 = up(sizeof(int32_t) * n), tmp_bytes = up(std::max(std::max(sort_tmp, sel_tmp), scan_tmp));
+    const size_t cell_bytes = up(sizeof(int) * (n_keys + 1));
     const size_t sort_bytes = sorted ? 4 * a4 + up(sizeof(int2) * n) + up(n) + tmp_bytes + up(sizeof(float4) * n) +
-                                           up(2 * sizeof(float4) * n)
+                                           up(2 * sizeof(float4) * n) + 2 * cell_bytes
                                      : 0;
     P2M_TRY(rest.ensure(rest_bytes + long_bytes + cnt_bytes + sort_bytes));
     char* base = rest.as<char>();
@@ -304,13 +328,18 @@ int run_query(p2m_index* h, MeshData& m, const float* d_pts, int64_t n, float* d
         float4* qs = reinterpret_cast<float4*>(p);
         p += up(sizeof(float4) * n);
         rec = reinterpret_cast<float4*>(p);
-        k_query_keys<<<blocks, threads, 0, s>>>(v, d_pts, n, k0, i0);
+        p += up(2 * sizeof(float4) * n);
+        int* cell_count = reinterpret_cast<int*>(p);
+        int* cell_first = reinterpret_cast<int*>(p + cell_bytes);
+        // queries in grid-cell Morton order, gathered into qs (counting sort)
+        P2M_CUDA_TRY(cudaMemsetAsync(cell_count, 0, sizeof(int) * (n_keys + 1), s));
+        k_cell_rank<<<blocks, threads, 0, s>>>(v, d_pts, n, (unsigned)n_keys, k0, i0, cell_count);
+        P2M_CUDA_TRY(cudaGetLastError());
+        P2M_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, scan_tmp, cell_count, cell_first, (int)(n_keys + 1), s));
+        k_cell_scatter<<<blocks, threads, 0, s>>>(d_pts, n, k0, i0, cell_first, qs);
         P2M_CUDA_TRY(cudaGetLastError());
         cub::DoubleBuffer<unsigned> dk(k0, k1);
         cub::DoubleBuffer<int32_t> dv(i0, i1);
-        P2M_CUDA_TRY(cub::DeviceRadixSort::SortPairs(tmp, sort_tmp, dk, dv, (int)n, 0, 24, s));
-        k_gather_points<<<blocks, threads, 0, s>>>(d_pts, dv.Current(), n, qs);
-        P2M_CUDA_TRY(cudaGetLastError());
         if (by_site) {
             // nearest sites in Morton order, then a stable sort by site (the Morton keys and the
             // permutation are dead once the points are gathered)
