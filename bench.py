@@ -132,6 +132,13 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(sm)}
 
 
+# Kernels of this library launched by one query pass (CUB's scan / select / sort kernels and
+# memsets not counted).  Sorted schedules 0 and 4: k_cell_rank, k_cell_scatter, the scan
+# kernel(s) (k_query_thread, or k_query_sites + k_query_scan), k_query_warp, k_split_records,
+# k_bvh_closest.  Schedules 1-3 (unsorted): k_query_thread, k_query_warp, k_bvh_closest.
+OWN_KERNELS_PER_STEP = {0: 6, 1: 3, 2: 3, 3: 3, 4: 7}
+
+
 def profiled_traffic(config, n):
     """DRAM bytes per query pass from the committed ncu summary of this workload, scaled to n
     queries, if the summary was taken on the current query-kernel sources (else None)."""
@@ -341,7 +348,7 @@ def main():
             "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": desc, "queries": n, "tris": mesh.n_tris, "l2": "flushed between steps (256 MB write)",
                        "parallelism": f"replicas x{world}" if world > 1 else "1 GPU"},
-            "gpu_launches": 3 * args.steps,
+            "gpu_launches": OWN_KERNELS_PER_STEP.get(args.schedule, 6) * args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": achieved / alu_peak, "traffic": profiled_traffic(args.config, n),
                          "kernel": "k_query_thread + k_query_warp (one query pass)",
