@@ -200,11 +200,11 @@ int p2m_mesh_distance(p2m_index* h, const float* d_verts_b, int64_t n_verts_b, c
 int p2m_mesh_distance_pair(p2m_index* a, p2m_index* b, int subdivisions, double* h_out, void* stream);
 
 /* The same query from host memory: copies h_pts in chunks to the device, runs the query
- * and copies the results back.  Host
- * buffers may be pageable, but pinned (cudaHostAlloc) buffers are much faster: chunks of
- * about n/8 points on three streams overlap the copies with the kernels.  Output
- * pointers other than h_dist may be NULL.  Synchronous: returns when the outputs are in
- * host memory.  Errors: INVALID_ARG, OOM, CUDA. */
+ * and copies the results back.  Host buffers may be pageable, but pinned (cudaHostAlloc)
+ * buffers are much faster: the chunks (pipe_chunks of the build parameters, 2 by default,
+ * at least 1M points each) run on separate streams, so one chunk's copies overlap another
+ * chunk's kernels.  Output pointers other than h_dist may be NULL.  Synchronous: returns
+ * when the outputs are in host memory.  Errors: INVALID_ARG, OOM, CUDA. */
 int p2m_query_host(p2m_index* h, const float* h_pts, int64_t n, float* h_dist, float* h_closest,
                    int32_t* h_tri, float* h_bary, void* stream);
 
