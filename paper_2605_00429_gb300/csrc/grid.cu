@@ -18,6 +18,7 @@ namespace p2m {
 
 constexpr int kKnn = 16;
 constexpr int kGridStack = 64;
+constexpr int kGridSlab = 16;  // candidates a cell keeps from the counting pass (~6 on average)
 
 struct GridParams {
     float3 lo;
@@ -86,13 +87,18 @@ __device__ __forceinline__ bool box_closer_to(float3 lo, float3 hi, float3 s, fl
     return v < -margin;
 }
 
+// Counting pass (FILL = false): count[cid] = the cell's candidates, the first kGridSlab of
+// them kept in slab[cid * kGridSlab ..].  Filling pass (FILL = true): the candidates of the
+// cells in `list` (those that overflowed the slab) written to out[off[cid] ..].
 template <bool FILL>
 __global__ void k_grid(GridParams g, const BNode* __restrict__ nodes, int root, const float4* __restrict__ sites,
-                       int n_sites, int64_t* __restrict__ count, const int64_t* __restrict__ off, float4* __restrict__ out,
-                       unsigned* status) {
+                       int n_sites, int64_t* __restrict__ count, float4* __restrict__ slab,
+                       const int64_t* __restrict__ list, int64_t n_list, const int64_t* __restrict__ off,
+                       float4* __restrict__ out, unsigned* status) {
     const int64_t n_cells = (int64_t)g.G * g.G * g.G;
-    for (int64_t cid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; cid < n_cells;
-         cid += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t n_work = FILL ? n_list : n_cells;
+    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_work; w += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t cid = FILL ? list[w] : w;
         const int ix = (int)(cid % g.G), iy = (int)((cid / g.G) % g.G), iz = (int)(cid / ((int64_t)g.G * g.G));
         const float3 c = cell_centre(g, ix, iy, iz);
         // the box is grown by 1% of a cell on every side: a query binned by FP32 rounding into
@@ -121,7 +127,9 @@ __global__ void k_grid(GridParams g, const BNode* __restrict__ nodes, int root, 
                 if (box_closer_to(lo, hi, ps, f3(__ldg(sites + t)), g.margin)) return;
             }
             // candidate stored with its coordinates (id in w) so a query reads one contiguous run
-            if (FILL) out[base + k] = make_float4(ps.x, ps.y, ps.z, __int_as_float(s));
+            const float4 e = make_float4(ps.x, ps.y, ps.z, __int_as_float(s));
+            if (FILL) out[base + k] = e;
+            else if (k < kGridSlab) slab[cid * kGridSlab + k] = e;
             ++k;
         };
         if (root < 0) {
@@ -153,6 +161,21 @@ __global__ void k_grid(GridParams g, const BNode* __restrict__ nodes, int root, 
 
 __global__ void k_i64_to_i32(const int64_t* __restrict__ a, int32_t* __restrict__ b, int64_t n);
 
+// Copies the slab-held candidates of every cell that fit into the slab to their CSR slots;
+// the cells that overflowed are appended to `list` for the filling pass.
+__global__ void k_grid_pack(const float4* __restrict__ slab, const int64_t* __restrict__ count,
+                            const int64_t* __restrict__ off, int64_t n_cells, float4* __restrict__ out,
+                            int64_t* __restrict__ list, unsigned long long* __restrict__ n_list) {
+    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = count[c];
+        if (k > kGridSlab) {
+            list[atomicAdd(n_list, 1ull)] = c;
+            continue;
+        }
+        for (int64_t j = 0; j < k; ++j) out[off[c] + j] = slab[c * kGridSlab + j];
+    }
+}
+
 int build_grid(MeshData& m, const Bvh& site_bvh, int G, unsigned* status, cudaStream_t s) {
     const int64_t n_cells = (int64_t)G * G * G;
     GridParams g;
@@ -169,8 +192,10 @@ int build_grid(MeshData& m, const Bvh& site_bvh, int G, unsigned* status, cudaSt
     const int n_sites = (int)(m.site_pos.size() / 3);
     const BNode* nodes = site_bvh.nodes.as<const BNode>();
     const int blocks = (int)std::min<int64_t>((n_cells + 127) / 128, 152 * 32);
+    DevBuf slab;
+    P2M_TRY(slab.alloc(sizeof(float4) * kGridSlab * n_cells));
     k_grid<false><<<blocks, 128, 0, s>>>(g, nodes, site_bvh.root, m.d_sites.as<float4>(), n_sites, cnt.as<int64_t>(),
-                                         nullptr, nullptr, status);
+                                         slab.as<float4>(), nullptr, 0, nullptr, nullptr, status);
     P2M_CUDA_TRY(cudaGetLastError());
     P2M_CUDA_TRY(cudaMemsetAsync(cnt.as<int64_t>() + n_cells, 0, sizeof(int64_t), s));
     DevBuf tmp;
@@ -184,9 +209,26 @@ int build_grid(MeshData& m, const Bvh& site_bvh, int G, unsigned* status, cudaSt
     if (total > 0x7fffffffLL) return fail(P2M_ERR_LIMIT, "nearest-site grid too large");
     P2M_TRY(m.d_cell_site.alloc(sizeof(float4) * std::max<int64_t>(total, 1)));
     P2M_TRY(m.d_cell_off.alloc(sizeof(int32_t) * (n_cells + 1)));
-    k_grid<true><<<blocks, 128, 0, s>>>(g, nodes, site_bvh.root, m.d_sites.as<float4>(), n_sites, nullptr,
-                                        off.as<int64_t>(), m.d_cell_site.as<float4>(), status);
+    // cells within the slab are copied; the rest (cells with more than kGridSlab candidates)
+    // run the search again, writing straight to their slots
+    DevBuf list, n_list;
+    P2M_TRY(list.alloc(sizeof(int64_t) * std::max<int64_t>(n_cells, 1)));
+    P2M_TRY(n_list.alloc(sizeof(unsigned long long)));
+    P2M_CUDA_TRY(cudaMemsetAsync(n_list.p, 0, sizeof(unsigned long long), s));
+    k_grid_pack<<<blocks, 128, 0, s>>>(slab.as<float4>(), cnt.as<int64_t>(), off.as<int64_t>(), n_cells,
+                                       m.d_cell_site.as<float4>(), list.as<int64_t>(), n_list.as<unsigned long long>());
     P2M_CUDA_TRY(cudaGetLastError());
+    unsigned long long n_over = 0;
+    P2M_CUDA_TRY(cudaMemcpyAsync(&n_over, n_list.p, sizeof(n_over), cudaMemcpyDeviceToHost, s));
+    P2M_CUDA_TRY(cudaStreamSynchronize(s));
+    slab.release();
+    if (n_over > 0) {
+        const int ob = (int)std::min<int64_t>(((int64_t)n_over + 127) / 128, 152 * 32);
+        k_grid<true><<<ob, 128, 0, s>>>(g, nodes, site_bvh.root, m.d_sites.as<float4>(), n_sites, nullptr, nullptr,
+                                        list.as<int64_t>(), (int64_t)n_over, off.as<int64_t>(),
+                                        m.d_cell_site.as<float4>(), status);
+        P2M_CUDA_TRY(cudaGetLastError());
+    }
     k_i64_to_i32<<<256, 256, 0, s>>>(off.as<int64_t>(), m.d_cell_off.as<int32_t>(), n_cells + 1);
     P2M_CUDA_TRY(cudaGetLastError());
     std::vector<int64_t> c(n_cells);
