@@ -139,9 +139,9 @@ class ClockSampler:
 OWN_KERNELS_PER_STEP = {0: 6, 1: 3, 2: 3, 3: 3, 4: 7}
 
 
-def profiled_traffic(config, n):
-    """DRAM bytes per query pass from the committed ncu summary of this workload, scaled to n
-    queries, if the summary was taken on the current query-kernel sources (else None)."""
+def profile_fields(config):
+    """The machine-readable fields ("- key: value" lines) of the committed ncu summary of this
+    workload, if it was taken on the current query-kernel sources (else an empty dict)."""
     import hashlib
     path = os.path.join(ROOT, "profiles", f"k_query_{config}.md")
     srcs = [os.path.join(ROOT, "paper_2605_00429_gb300", "csrc", f) for f in ("query.cu", "query_dev.cuh", "geom.cuh")]
@@ -152,10 +152,25 @@ def profiled_traffic(config, n):
             if ":" in line and line.startswith("- "):
                 k, v = line[2:].split(":", 1)
                 fields[k.strip()] = v.strip()
-        if fields.get("source_sha256_16") != h:
-            return None
-        return float(fields["dram_bytes_per_query"]) * n
-    except (OSError, KeyError, ValueError):
+    except OSError:
+        return {}
+    return fields if fields.get("source_sha256_16") == h else {}
+
+
+def profiled_traffic(config, n):
+    """DRAM bytes per query pass from the committed ncu summary, scaled to n queries (None if
+    the summary is not of the current sources)."""
+    try:
+        return float(profile_fields(config)["dram_bytes_per_query"]) * n
+    except (KeyError, ValueError):
+        return None
+
+
+def profiled_l1tex_pct(config):
+    """L1TEX throughput of k_query_thread (% of peak) in the same summary, or None."""
+    try:
+        return float(profile_fields(config)["l1tex_throughput_pct"])
+    except (KeyError, ValueError):
         return None
 
 
@@ -351,6 +366,7 @@ def main():
             "gpu_launches": OWN_KERNELS_PER_STEP.get(args.schedule, 6) * args.steps,
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": achieved / alu_peak, "traffic": profiled_traffic(args.config, n),
+                         "l1tex_pct_ncu": profiled_l1tex_pct(args.config),
                          "kernel": "k_query_thread + k_query_warp (one query pass)",
                          "peak_kind": f"FP32 FMA lanes x max SM clock from {pk_kind} peaks",
                          "hbm_achieved_gbs": hbm_gbs, "hbm_peak_gbs": pk.get("hbm_gbs"),
