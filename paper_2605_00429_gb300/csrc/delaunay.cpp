@@ -16,8 +16,10 @@
 #include "host_geom.h"
 
 #include <algorithm>
+#include <atomic>
+#include <thread>
+#include <cmath>
 #include <cstring>
-#include <unordered_map>
 
 namespace p2m {
 
@@ -25,15 +27,27 @@ using i128 = __int128;
 
 static inline int sgn(i128 v) { return (v > 0) - (v < 0); }
 
+// Both predicates first evaluate their determinant in double with a static error bound
+// and fall back to exact __int128 arithmetic only when the sign is not certain.  All
+// coordinate differences are below 2^24 in magnitude (|x| <= 12 * 2^19), so every 2x2 minor
+// below is an exact int64 (< 2^49) and converts to double exactly; the double sums then
+// carry a relative error below a few units of 2^-53 of the sum of the absolute terms, and
+// the bounds used (2^-50 and 2^-49 of those sums) exceed it with margin.
+
 // orient3d(a,b,c,d) = det[b-a, c-a, d-a]: > 0 if d is on the side of plane (a,b,c) that the
 // normal (b-a) x (c-a) points to.
 static inline int orient3d(const IPt& a, const IPt& b, const IPt& c, const IPt& d) {
     const int64_t bx = b.x - a.x, by = b.y - a.y, bz = b.z - a.z;
     const int64_t cx = c.x - a.x, cy = c.y - a.y, cz = c.z - a.z;
     const int64_t dx = d.x - a.x, dy = d.y - a.y, dz = d.z - a.z;
-    const i128 m0 = (i128)cy * dz - (i128)cz * dy;
-    const i128 m1 = (i128)cz * dx - (i128)cx * dz;
-    const i128 m2 = (i128)cx * dy - (i128)cy * dx;
+    const int64_t m0 = cy * dz - cz * dy;
+    const int64_t m1 = cz * dx - cx * dz;
+    const int64_t m2 = cx * dy - cy * dx;
+    const double p0 = (double)bx * (double)m0, p1 = (double)by * (double)m1, p2 = (double)bz * (double)m2;
+    const double det = p0 + p1 + p2;
+    const double bound = (std::fabs(p0) + std::fabs(p1) + std::fabs(p2)) * 0x1p-50;
+    if (det > bound) return 1;
+    if (det < -bound) return -1;
     return sgn((i128)bx * m0 + (i128)by * m1 + (i128)bz * m2);
 }
 
@@ -41,9 +55,27 @@ static inline int orient3d(const IPt& a, const IPt& b, const IPt& c, const IPt& 
 static inline int insphere(const IPt& a, const IPt& b, const IPt& c, const IPt& d, const IPt& e) {
     const int64_t r[4][3] = {{a.x - e.x, a.y - e.y, a.z - e.z}, {b.x - e.x, b.y - e.y, b.z - e.z},
                              {c.x - e.x, c.y - e.y, c.z - e.z}, {d.x - e.x, d.y - e.y, d.z - e.z}};
-    i128 w[4];
-    for (int i = 0; i < 4; ++i) w[i] = (i128)r[i][0] * r[i][0] + (i128)r[i][1] * r[i][1] + (i128)r[i][2] * r[i][2];
-    // 3x3 minors of the coordinate rows, expansion along the lifted column
+    int64_t w[4];
+    for (int i = 0; i < 4; ++i) w[i] = r[i][0] * r[i][0] + r[i][1] * r[i][1] + r[i][2] * r[i][2];
+    // 3x3 minors of the coordinate rows (expansion along the lifted column): the 2x2 minors
+    // exactly, the 3x3 value in double with the sum of its absolute terms
+    auto m3d = [&](int i, int j, int k, double& perm) -> double {
+        const int64_t a0 = r[j][1] * r[k][2] - r[j][2] * r[k][1];
+        const int64_t a1 = r[j][2] * r[k][0] - r[j][0] * r[k][2];
+        const int64_t a2 = r[j][0] * r[k][1] - r[j][1] * r[k][0];
+        const double q0 = (double)r[i][0] * (double)a0, q1 = (double)r[i][1] * (double)a1,
+                     q2 = (double)r[i][2] * (double)a2;
+        perm = std::fabs(q0) + std::fabs(q1) + std::fabs(q2);
+        return q0 + q1 + q2;
+    };
+    double e0, e1, e2, e3;
+    const double n0 = m3d(1, 2, 3, e0), n1 = m3d(0, 2, 3, e1), n2 = m3d(0, 1, 3, e2), n3 = m3d(0, 1, 2, e3);
+    const double t0 = (double)w[0] * n0, t1 = (double)w[1] * n1, t2 = (double)w[2] * n2, t3 = (double)w[3] * n3;
+    const double detd = -t0 + t1 - t2 + t3;
+    const double bound = ((double)w[0] * e0 + (double)w[1] * e1 + (double)w[2] * e2 + (double)w[3] * e3) * 0x1p-49;
+    // for a positively oriented tet the determinant is negative for an inside point
+    if (detd > bound) return -1;
+    if (detd < -bound) return 1;
     auto m3 = [&](int i, int j, int k) -> i128 {
         const i128 a0 = (i128)r[j][1] * r[k][2] - (i128)r[j][2] * r[k][1];
         const i128 a1 = (i128)r[j][2] * r[k][0] - (i128)r[j][0] * r[k][2];
@@ -51,8 +83,8 @@ static inline int insphere(const IPt& a, const IPt& b, const IPt& c, const IPt& 
         return (i128)r[i][0] * a0 + (i128)r[i][1] * a1 + (i128)r[i][2] * a2;
     };
     // det of rows (r_i, w_i): sum_i (-1)^(i+3) w_i M_i
-    const i128 det = -w[0] * m3(1, 2, 3) + w[1] * m3(0, 2, 3) - w[2] * m3(0, 1, 3) + w[3] * m3(0, 1, 2);
-    // for a positively oriented tet this determinant is negative for an inside point
+    const i128 det = -(i128)w[0] * m3(1, 2, 3) + (i128)w[1] * m3(0, 2, 3) - (i128)w[2] * m3(0, 1, 3) +
+                     (i128)w[3] * m3(0, 1, 2);
     return -sgn(det);
 }
 
@@ -170,7 +202,6 @@ int Delaunay::insert(const IPt& q, uint64_t& rng) {
     pts.push_back(q);
     // create new tets; the boundary faces keep their outer neighbours
     created.clear();
-    std::vector<std::pair<int, int>> old_face;  // (tet, face) of the outer neighbour side
     for (const auto& b : boundary) {
         const Tet T = tets[b.first];
         const int* f = kFace[b.second];
@@ -197,53 +228,91 @@ int Delaunay::insert(const IPt& q, uint64_t& rng) {
         free_list.push_back(t);
     }
     // Note: new_tet() above could not reuse cavity tets because they were freed afterwards.
-    // link new tets to each other through their edges on the cavity boundary
-    edge_map.clear();
+    // link new tets to each other through their edges on the cavity boundary: every such
+    // edge is shared by exactly two new tets.  An open-addressing table keyed by the edge
+    // pairs them; its slots carry the insertion's stamp, so nothing is cleared per point.
+    const size_t need = 4 * 3 * created.size();
+    if (htab.size() < need) {
+        size_t sz = 64;
+        while (sz < need) sz <<= 1;
+        htab.assign(sz, HSlot());
+        hstamp = 0;
+    }
+    if (++hstamp == 0) {
+        for (HSlot& h : htab) h.stamp = 0;
+        hstamp = 1;
+    }
+    const size_t mask = htab.size() - 1;
+    int open_edges = 0;
     for (int nt : created) {
-        Tet& N = tets[nt];
+        const Tet& N = tets[nt];
         for (int k = 0; k < 3; ++k) {
             // face opposite N.v[k] contains q and the edge of the other two base vertices
             const int a = N.v[(k + 1) % 3], b = N.v[(k + 2) % 3];
             const uint64_t key = a < b ? ((uint64_t)a << 32 | (uint32_t)b) : ((uint64_t)b << 32 | (uint32_t)a);
-            auto it = edge_map.find(key);
-            if (it == edge_map.end()) {
-                edge_map.emplace(key, std::make_pair(nt, k));
+            size_t h = (size_t)((key * 0x9E3779B97F4A7C15ull) >> 32) & mask;
+            while (htab[h].stamp == hstamp && htab[h].key != key) h = (h + 1) & mask;
+            HSlot& e = htab[h];
+            if (e.stamp != hstamp) {
+                e = {key, nt, k, hstamp, 1};
+                ++open_edges;
             } else {
-                tets[it->second.first].n[it->second.second] = nt;
-                N.n[k] = it->second.first;
-                edge_map.erase(it);
+                if (++e.count > 2) return INSERT_BROKEN;
+                tets[e.tet].n[e.face] = nt;
+                tets[nt].n[k] = e.tet;
+                --open_edges;
             }
         }
     }
-    if (!edge_map.empty()) return INSERT_BROKEN;
+    if (open_edges != 0) return INSERT_BROKEN;
     last = created.empty() ? last : created.back();
     return qi;
 }
 
-void Delaunay::neighbours(int n_real, std::vector<int64_t>& off, std::vector<int32_t>& nb) const {
-    // collect unique real-real edges, then CSR by vertex (ids shifted by n_super)
-    std::vector<std::pair<int32_t, int32_t>> e;
-    e.reserve(tets.size() * 6);
+void Delaunay::neighbours(int n_real, std::vector<int64_t>& off, std::vector<int32_t>& nb, int n_threads) const {
+    // every live tet lists, for each real vertex, its other real vertices; each vertex's list
+    // (with repeats: an edge lies in several tets) is then sorted and deduplicated, threads
+    // splitting the vertices.  Ids are shifted by n_super.
+    std::vector<int64_t> cnt(n_real + 1, 0);
     for (const Tet& T : tets) {
         if (!T.alive) continue;
+        int real = 0;
+        for (int i = 0; i < 4; ++i) real += T.v[i] >= n_super;
         for (int i = 0; i < 4; ++i)
-            for (int j = i + 1; j < 4; ++j) {
-                const int a = T.v[i] - n_super, b = T.v[j] - n_super;
-                if (a < 0 || b < 0) continue;
-                e.push_back({std::min(a, b), std::max(a, b)});
+            if (T.v[i] >= n_super) cnt[T.v[i] - n_super + 1] += real - 1;
+    }
+    for (int i = 0; i < n_real; ++i) cnt[i + 1] += cnt[i];
+    std::vector<int32_t> all(cnt[n_real]);
+    std::vector<int64_t> pos(cnt.begin(), cnt.end() - 1);
+    for (const Tet& T : tets) {
+        if (!T.alive) continue;
+        for (int i = 0; i < 4; ++i) {
+            if (T.v[i] < n_super) continue;
+            for (int j = 0; j < 4; ++j)
+                if (j != i && T.v[j] >= n_super) all[pos[T.v[i] - n_super]++] = T.v[j] - n_super;
+        }
+    }
+    std::vector<int64_t> len(n_real, 0);
+    std::atomic<int> next(0);
+    auto work = [&]() {
+        while (true) {
+            const int v0 = next.fetch_add(1024);
+            if (v0 >= n_real) break;
+            for (int v = v0; v < std::min(n_real, v0 + 1024); ++v) {
+                int32_t* b = all.data() + cnt[v];
+                int32_t* e = all.data() + cnt[v + 1];
+                std::sort(b, e);
+                len[v] = std::unique(b, e) - b;
             }
-    }
-    std::sort(e.begin(), e.end());
-    e.erase(std::unique(e.begin(), e.end()), e.end());
+        }
+    };
+    std::vector<std::thread> th;
+    for (int t = 0; t < std::max(1, n_threads); ++t) th.emplace_back(work);
+    for (auto& t : th) t.join();
     off.assign(n_real + 1, 0);
-    for (auto& p : e) { off[p.first + 1]++; off[p.second + 1]++; }
-    for (int i = 0; i < n_real; ++i) off[i + 1] += off[i];
+    for (int v = 0; v < n_real; ++v) off[v + 1] = off[v] + len[v];
     nb.resize(off[n_real]);
-    std::vector<int64_t> pos(off.begin(), off.end() - 1);
-    for (auto& p : e) {
-        nb[pos[p.first]++] = p.second;
-        nb[pos[p.second]++] = p.first;
-    }
+    for (int v = 0; v < n_real; ++v) std::copy(all.begin() + cnt[v], all.begin() + cnt[v] + len[v], nb.begin() + off[v]);
 }
 
 int64_t Delaunay::count_real_tets() const {

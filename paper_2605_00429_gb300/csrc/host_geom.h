@@ -3,7 +3,6 @@
 #pragma once
 
 #include <cstdint>
-#include <unordered_map>
 #include <utility>
 #include <vector>
 
@@ -31,8 +30,9 @@ public:
     // Insert q; returns its vertex id (>= 4) or INSERT_* on failure (nothing changed for
     // DUPLICATE and FLAT).
     int insert(const IPt& q, uint64_t& rng);
-    // Delaunay neighbours of the real points (ids 0..n_real-1 = vertex id - 4), CSR.
-    void neighbours(int n_real, std::vector<int64_t>& off, std::vector<int32_t>& nb) const;
+    // Delaunay neighbours of the real points (ids 0..n_real-1 = vertex id - 4), CSR, each
+    // list ascending; n_threads threads sort the lists.
+    void neighbours(int n_real, std::vector<int64_t>& off, std::vector<int32_t>& nb, int n_threads) const;
     int64_t count_real_tets() const;
     void circumcentres(std::vector<double>& out) const;
     int validate(bool full) const;
@@ -46,7 +46,13 @@ private:
     std::vector<unsigned> mark;
     unsigned epoch = 1;
     int last = 0;
-    std::unordered_map<uint64_t, std::pair<int, int>> edge_map;
+    struct HSlot {
+        uint64_t key = 0;  // cavity-boundary edge (lower vertex id << 32 | higher)
+        int tet = 0, face = 0;
+        unsigned stamp = 0, count = 0;
+    };
+    std::vector<HSlot> htab;
+    unsigned hstamp = 0;
 };
 
 // Convex polytope clipping in FP64: returns the corners of D ∩ {x : (x - m_k) . n_k <= 0}.

@@ -69,22 +69,28 @@ void SiteSet::neighbour_csr() {
     for (int i = 0; i < (int)vid.size(); ++i) site_of[vid[i]] = i;
     std::vector<int64_t> off;
     std::vector<int32_t> nb;
-    dt.neighbours((int)dt.pts.size() - dt.n_super, off, nb);
+    dt.neighbours((int)dt.pts.size() - dt.n_super, off, nb, hardware_threads());
     const int n = (int)pts.size();
+    const int nv = (int)dt.pts.size() - dt.n_super;
+    // CSR over sites straight from the CSR over Delaunay vertices
     nb_off.assign(n + 1, 0);
-    nb_id.clear();
-    std::vector<std::vector<int32_t>> tmp(n);
-    for (int v = 0; v + dt.n_super < (int)dt.pts.size(); ++v) {
+    for (int v = 0; v < nv; ++v) {
         const int s = site_of[v + dt.n_super];
         if (s < 0) continue;
+        int64_t c = 0;
+        for (int64_t k = off[v]; k < off[v + 1]; ++k) c += site_of[nb[k] + dt.n_super] >= 0;
+        nb_off[s + 1] = c;
+    }
+    for (int s = 0; s < n; ++s) nb_off[s + 1] += nb_off[s];
+    nb_id.assign(nb_off[n], 0);
+    for (int v = 0; v < nv; ++v) {
+        const int s = site_of[v + dt.n_super];
+        if (s < 0) continue;
+        int64_t w = nb_off[s];
         for (int64_t k = off[v]; k < off[v + 1]; ++k) {
             const int t = site_of[nb[k] + dt.n_super];
-            if (t >= 0) tmp[s].push_back(t);
+            if (t >= 0) nb_id[w++] = t;
         }
-    }
-    for (int s = 0; s < n; ++s) {
-        nb_off[s + 1] = nb_off[s] + (int64_t)tmp[s].size();
-        nb_id.insert(nb_id.end(), tmp[s].begin(), tmp[s].end());
     }
     // each site's neighbours nearest first (squared distance, then id): the order both cell
     // clippers cut in
