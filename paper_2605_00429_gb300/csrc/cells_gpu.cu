@@ -4,8 +4,9 @@
 // order (nearest first, as the neighbour lists are stored), tolerance rule and early stop
 // as the host clipper, so both produce the same cell up to rounding.
 //
-// Representation: the cell's dual.  Each face plane is stored once (n, d), and each corner
-// is a triangle of the three planes through it, together with its position.  Keeping the
+// Representation: the cell's dual.  Each face plane has an index (0..5 for the box, then one
+// per cut), and each corner is a triangle of the three planes through it, together with its
+// position; the planes themselves need not be kept, since new corners are interpolated.  Keeping the
 // triangles consistently oriented (det(n_a, n_b, n_c) > 0 for the box corners, and inherited
 // from the removed triangle for new ones) makes every directed edge (a -> b) appear in
 // exactly one triangle and (b -> a) in its neighbour, which is all a clip needs:
@@ -44,10 +45,9 @@ __host__ __device__ __forceinline__ int tri_pack(int a, int b, int c) { return a
 __host__ __device__ __forceinline__ int tri_at(int t, int k) { return (t >> (8 * k)) & 0xff; }
 
 struct CellPoly {
-    Plane pl[kCellPlanes];
     int tri[kCellTris];
     double3 pos[kCellTris];
-    int np, nt;
+    int np, nt;  // planes used (box + cuts), corners
 };
 
 __host__ __device__ __forceinline__ double plane_val(const Plane& p, const double3& x) {
@@ -56,12 +56,6 @@ __host__ __device__ __forceinline__ double plane_val(const Plane& p, const doubl
 
 __host__ __device__ void cell_box(CellPoly& C, double3 lo, double3 hi) {
     // planes 0..5: x <= hi.x, -x <= -lo.x, y <= hi.y, -y <= -lo.y, z <= hi.z, -z <= -lo.z
-    C.pl[0] = Plane{1, 0, 0, hi.x};
-    C.pl[1] = Plane{-1, 0, 0, -lo.x};
-    C.pl[2] = Plane{0, 1, 0, hi.y};
-    C.pl[3] = Plane{0, -1, 0, -lo.y};
-    C.pl[4] = Plane{0, 0, 1, hi.z};
-    C.pl[5] = Plane{0, 0, -1, -lo.z};
     C.np = 6;
     C.nt = 8;
     for (int i = 0; i < 8; ++i) {
@@ -153,7 +147,7 @@ __host__ __device__ int cell_clip(CellPoly& C, double3 n, double d, double tol) 
         ++w;
     }
     C.nt = w;
-    C.pl[C.np++] = P;
+    ++C.np;
     return 1;
 }
 
