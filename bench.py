@@ -33,7 +33,10 @@ import p2m_workloads as W  # noqa: E402
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
 SM_COUNT = 152
 FP32_LANES_PER_SM = 128
-# algorithmic FP32 work model (FLOP, an FMA counts 2): see DESIGN.md "Roofline"
+# algorithmic FP32 work model (FLOP, an FMA counts 2): a candidate site is a squared
+# distance and a compare, a list entry the bounding-sphere test, an exact test the weighted
+# mix of the interior and edge paths of the point-triangle distance, and a query its fixed
+# grid lookup, bound setup and result
 FLOP_PER_SITE = 8
 FLOP_PER_ROW_ENTRY = 10
 FLOP_PER_EXACT = 80
