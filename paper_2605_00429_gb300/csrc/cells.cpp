@@ -20,7 +20,13 @@ void Clipper::box(const double lo[3], const double hi[3]) {
         V.push_back((i & 2) ? hi[1] : lo[1]);
         V.push_back((i & 4) ? hi[2] : lo[2]);
     }
-    F = {{0, 2, 6, 4}, {1, 5, 7, 3}, {0, 4, 5, 1}, {2, 3, 7, 6}, {0, 1, 3, 2}, {4, 6, 7, 5}};
+    static const int kBoxFaces[6][4] = {{0, 2, 6, 4}, {1, 5, 7, 3}, {0, 4, 5, 1}, {2, 3, 7, 6}, {0, 1, 3, 2}, {4, 6, 7, 5}};
+    fidx.clear();
+    foff.assign(1, 0);
+    for (const auto& f : kBoxFaces) {
+        fidx.insert(fidx.end(), f, f + 4);
+        foff.push_back((int)fidx.size());
+    }
 }
 
 double Clipper::radius_from(const double p[3]) const { return std::sqrt(radius2_from(p)); }
@@ -45,7 +51,8 @@ bool Clipper::clip(const double n[3], double d, double tol) {
     if (n_out == 0) return true;
     if (n_out == nv) {
         V.clear();
-        F.clear();
+        fidx.clear();
+        foff.assign(1, 0);
         return false;
     }
     edge_new.clear();
@@ -63,32 +70,34 @@ bool Clipper::clip(const double n[3], double d, double tol) {
         return id;
     };
     cap.clear();
-    std::vector<std::vector<int>> nf;
-    nf.reserve(F.size() + 1);
-    std::vector<int> poly;
-    for (const auto& f : F) {
-        poly.clear();
-        const int k = (int)f.size();
+    nfidx.clear();
+    nfoff.assign(1, 0);
+    const int n_faces = (int)foff.size() - 1;
+    for (int fi = 0; fi < n_faces; ++fi) {
+        const int* f = fidx.data() + foff[fi];
+        const int k = foff[fi + 1] - foff[fi];
+        // the kept part of the face, consecutive duplicates dropped, straight into nfidx
+        const size_t start = nfidx.size();
+        auto put = [&](int v) {
+            if (nfidx.size() == start || nfidx.back() != v) nfidx.push_back(v);
+        };
         for (int j = 0; j < k; ++j) {
             const int a = f[j], b = f[(j + 1) % k];
             const bool ain = val[a] <= tol, bin = val[b] <= tol;
-            if (ain) poly.push_back(a);
+            if (ain) put(a);
             if (ain && !bin) {
                 const int c = cut_vertex(a, b);
-                if (c != a) poly.push_back(c);
+                if (c != a) put(c);
                 cap.push_back(c);
             } else if (!ain && bin) {
                 const int c = cut_vertex(b, a);
-                if (c != b) poly.push_back(c);
+                if (c != b) put(c);
                 cap.push_back(c);
             }
         }
-        // drop consecutive duplicates
-        std::vector<int> q;
-        for (int v : poly)
-            if (q.empty() || q.back() != v) q.push_back(v);
-        if (q.size() > 1 && q.front() == q.back()) q.pop_back();
-        if (q.size() >= 3) nf.push_back(q);
+        if (nfidx.size() - start > 1 && nfidx[start] == nfidx.back()) nfidx.pop_back();
+        if (nfidx.size() - start >= 3) nfoff.push_back((int)nfidx.size());
+        else nfidx.resize(start);
     }
     // the cap face: the cut vertices, ordered by angle about their centroid in the plane
     std::sort(cap.begin(), cap.end());
@@ -105,31 +114,30 @@ bool Clipper::clip(const double n[3], double d, double tol) {
         t[(ax <= ay && ax <= az) ? 0 : (ay <= az ? 1 : 2)] = 1.0;
         u[0] = n[1] * t[2] - n[2] * t[1]; u[1] = n[2] * t[0] - n[0] * t[2]; u[2] = n[0] * t[1] - n[1] * t[0];
         w[0] = n[1] * u[2] - n[2] * u[1]; w[1] = n[2] * u[0] - n[0] * u[2]; w[2] = n[0] * u[1] - n[1] * u[0];
-        std::vector<std::pair<double, int>> ang;
+        ang.clear();
         for (int v : cap) {
             const double d0 = V[3 * v] - c[0], d1 = V[3 * v + 1] - c[1], d2 = V[3 * v + 2] - c[2];
             ang.push_back({std::atan2(d0 * w[0] + d1 * w[1] + d2 * w[2], d0 * u[0] + d1 * u[1] + d2 * u[2]), v});
         }
         std::sort(ang.begin(), ang.end());
-        std::vector<int> q;
-        for (auto& p : ang) q.push_back(p.second);
-        nf.push_back(q);
+        for (auto& p : ang) nfidx.push_back(p.second);
+        nfoff.push_back((int)nfidx.size());
     }
-    // compact: keep vertices used by some face
+    // compact: keep vertices used by some face, numbered in order of first use
     const int nv2 = n_verts();
     remap.assign(nv2, -1);
-    std::vector<double> V2;
-    for (auto& f : nf)
-        for (int& v : f) {
-            if (remap[v] < 0) {
-                remap[v] = (int)(V2.size() / 3);
-                for (int k = 0; k < 3; ++k) V2.push_back(V[3 * v + k]);
-            }
-            v = remap[v];
+    V2.clear();
+    for (int& v : nfidx) {
+        if (remap[v] < 0) {
+            remap[v] = (int)(V2.size() / 3);
+            for (int k = 0; k < 3; ++k) V2.push_back(V[3 * v + k]);
         }
+        v = remap[v];
+    }
     V.swap(V2);
-    F.swap(nf);
-    return !F.empty();
+    fidx.swap(nfidx);
+    foff.swap(nfoff);
+    return foff.size() > 1;
 }
 
 bool Lattice::setup(const double dom_lo[3], const double dom_hi[3]) {

@@ -58,7 +58,7 @@ private:
 // Convex polytope clipping in FP64: returns the corners of D ∩ {x : (x - m_k) . n_k <= 0}.
 struct Clipper {
     std::vector<double> V;                 // xyz
-    std::vector<std::vector<int>> F;       // faces as cyclic vertex-id lists
+    std::vector<int> fidx, foff;           // faces as cyclic vertex-id lists (CSR)
     void box(const double lo[3], const double hi[3]);
     // keep the half-space n . x <= d; returns false if the polytope became empty
     bool clip(const double n[3], double d, double tol);
@@ -67,10 +67,11 @@ struct Clipper {
     int n_verts() const { return (int)(V.size() / 3); }
 
 private:
-    std::vector<double> val;
-    std::vector<int> remap;
+    std::vector<double> val, V2;
+    std::vector<int> remap, nfidx, nfoff;
     std::vector<std::pair<uint64_t, int>> edge_new;
     std::vector<int> cap;
+    std::vector<std::pair<double, int>> ang;
 };
 
 // Lattice that maps FP32-exact site positions to small integers: x = (c + k) * h, with
