@@ -4,6 +4,8 @@
 //   and Eq. 8, the interception lists (K1, lists.cu) and the nearest-site grid (K2a,
 //   grid.cu).
 #include <algorithm>
+#include <thread>
+#include <atomic>
 #include <array>
 #include <chrono>
 #include <cmath>
@@ -365,14 +367,16 @@ int build_partition(MeshData& m, const p2m_build_params& prm, p2m_index* h, cuda
         P2M_CUDA_TRY(cudaStreamSynchronize(s));
     }
     // corner balls (Eq. 3 for vertex sites, Eq. 8 for auxiliary sites); a ball contained in
-    // another ball of the same site adds nothing to the union and is dropped
+    // another ball of the same site adds nothing to the union and is dropped.  Sites are
+    // independent: threads build each site's balls, which are then concatenated in order.
     m.ball_off.assign(S + 1, 0);
     m.ball_c.clear();
     m.ball_r.clear();
     {
-        std::vector<double> uc, ur;
-        std::vector<char> keep;
-        for (int i = 0; i < S; ++i) {
+        std::vector<std::vector<double>> site_c(S), site_r(S);
+        auto site_balls = [&](int i, std::vector<double>& uc, std::vector<double>& ur, std::vector<char>& keep) {
+            std::vector<double>& out_c = site_c[i];
+            std::vector<double>& out_r = site_r[i];
             const double* v = &m.site_ref[3 * i];
             const int64_t c0 = ss.cell_off[i], c1 = ss.cell_off[i + 1];
             uc.clear();
@@ -399,8 +403,8 @@ int build_partition(MeshData& m, const p2m_build_params& prm, p2m_index* h, cuda
                     if (keep[a]) kept.push_back(a);
                 if ((int)kept.size() <= kMaxBalls) {
                     for (int a : kept) {
-                        m.ball_c.insert(m.ball_c.end(), &uc[3 * a], &uc[3 * a] + 3);
-                        m.ball_r.push_back(ur[a]);
+                        out_c.insert(out_c.end(), &uc[3 * a], &uc[3 * a] + 3);
+                        out_r.push_back(ur[a]);
                     }
                 } else {
                     // Too many corners (cells reaching a degenerate region have hundreds):
@@ -442,8 +446,8 @@ int build_partition(MeshData& m, const p2m_build_params& prm, p2m_index* h, cuda
                     }
                     for (int c = 0; c < kMaxBalls; ++c) {
                         const double* pc = &uc[3 * kept[centre[c]]];
-                        m.ball_c.insert(m.ball_c.end(), pc, pc + 3);
-                        m.ball_r.push_back(R[c]);
+                        out_c.insert(out_c.end(), pc, pc + 3);
+                        out_r.push_back(R[c]);
                     }
                 }
             } else {
@@ -456,9 +460,26 @@ int build_partition(MeshData& m, const p2m_build_params& prm, p2m_index* h, cuda
                     const double b = std::sqrt((u[0] - v[0]) * (u[0] - v[0]) + (u[1] - v[1]) * (u[1] - v[1]) + (u[2] - v[2]) * (u[2] - v[2]));
                     r = std::max(r, a + b);
                 }
-                m.ball_c.insert(m.ball_c.end(), p, p + 3);
-                m.ball_r.push_back(r);
+                out_c.insert(out_c.end(), p, p + 3);
+                out_r.push_back(r);
             }
+        };
+        std::atomic<int> next(0);
+        auto work = [&]() {
+            std::vector<double> uc, ur;
+            std::vector<char> keep;
+            while (true) {
+                const int i0 = next.fetch_add(256);
+                if (i0 >= S) break;
+                for (int i = i0; i < std::min(S, i0 + 256); ++i) site_balls(i, uc, ur, keep);
+            }
+        };
+        std::vector<std::thread> th;
+        for (int t = 0; t < std::max(1, std::min(hardware_threads(), (S + 255) / 256)); ++t) th.emplace_back(work);
+        for (auto& t : th) t.join();
+        for (int i = 0; i < S; ++i) {
+            m.ball_c.insert(m.ball_c.end(), site_c[i].begin(), site_c[i].end());
+            m.ball_r.insert(m.ball_r.end(), site_r[i].begin(), site_r[i].end());
             m.ball_off[i + 1] = (int64_t)m.ball_r.size();
         }
     }
