@@ -142,14 +142,27 @@ class ClockSampler:
 OWN_KERNELS_PER_STEP = {0: 6, 1: 3, 2: 3, 3: 3, 4: 7}
 
 
+def query_source_hash():
+    """First 16 hex digits of the SHA-256 of the query-kernel sources (query.cu,
+    query_dev.cuh, geom.cuh) with comments and blank lines removed: the code the profiled
+    kernels were compiled from."""
+    import hashlib
+    import re
+
+    def strip(src):
+        src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+        src = re.sub(r"//[^\n]*", "", src)
+        return "\n".join(line.rstrip() for line in src.splitlines() if line.strip())
+    srcs = [os.path.join(ROOT, "paper_2605_00429_gb300", "csrc", f) for f in ("query.cu", "query_dev.cuh", "geom.cuh")]
+    return hashlib.sha256("\n".join(strip(open(f).read()) for f in srcs).encode()).hexdigest()[:16]
+
+
 def profile_fields(config):
     """The machine-readable fields ("- key: value" lines) of the committed ncu summary of this
-    workload, if it was taken on the current query-kernel sources (else an empty dict)."""
-    import hashlib
+    workload, if it was taken on the current query-kernel code (else an empty dict)."""
     path = os.path.join(ROOT, "profiles", f"k_query_{config}.md")
-    srcs = [os.path.join(ROOT, "paper_2605_00429_gb300", "csrc", f) for f in ("query.cu", "query_dev.cuh", "geom.cuh")]
     try:
-        h = hashlib.sha256(b"".join(open(f, "rb").read() for f in srcs)).hexdigest()[:16]
+        h = query_source_hash()
         fields = {}
         for line in open(path):
             if ":" in line and line.startswith("- "):

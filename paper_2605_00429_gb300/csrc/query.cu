@@ -1,12 +1,16 @@
 // Query path (Section 3.3 "Distance Query Stage"):
+//   order  the queries are counting-sorted by the Morton code of their grid cell, so that
+//       neighbouring threads read the same candidate and interception lists; each result
+//       leaves as a 32-byte record at the query's index, split into the outputs at the end.
 //   K2  nearest site: one grid lookup, an FP32 scan of the cell's candidate sites, and an
 //       FP64 re-check when the two best are within 4e-6 (relative, squared) of each other;
 //       ties go to the lower site index.
 //   K3  list scan: the site's interception list, with bounding-sphere pruning ("Bounding
-//       Sphere Pruning"): a triangle is tested exactly only if ||q - c|| - r does not exceed
-//       the current bound.  The bound starts at the distance to the site's reference point on
-//       the mesh (an upper bound of d(q, M)), so pruning works from the first entry.  The
-//       minimum is taken over (squared distance, triangle id).
+//       Sphere Pruning"): a triangle is tested exactly only if ||q - c|| - r, and a tighter
+//       bound combining its plane and its sphere, do not exceed the current bound.  The
+//       bound starts at the distance to the site's reference point on the mesh (an upper
+//       bound of d(q, M)), so pruning works from the first entry; short lists are sorted so
+//       the scan can stop early.  The minimum is taken over (squared distance, triangle id).
 //   K5  points outside the domain box D (or, defensively, whose list gave no triangle) are
 //       compacted and answered by the exact BVH search.
 #include <cub/device/device_radix_sort.cuh>
@@ -66,8 +70,9 @@ __global__ void __launch_bounds__(256, 6) k_query_thread(MeshView m, const float
     }
 }
 
-// Sorted order, first step: the points in sorted order with their index in .w, so that the
-// query kernels read them coalesced (the random gather runs here, in a streaming kernel).
+// Batched path, after its radix sort: the points in sorted order with their index in .w,
+// so that the query kernels read them coalesced (the random gather runs here, in a
+// streaming kernel).
 __global__ void k_gather_points(const float* __restrict__ pts, const int32_t* __restrict__ perm, int64_t n,
                                 float4* __restrict__ qs) {
     for (int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
