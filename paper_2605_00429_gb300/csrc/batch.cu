@@ -264,9 +264,9 @@ int run_batch_query(p2m_index* h, const float* d_pts, const int64_t* h_off, floa
         // autotuner: time each (tile, long_row) candidate on this batch, keep the fastest
         const int tiles[] = {1024, 4096};
         const int longs[] = {0, 64, 256, 1024};
-        cudaEvent_t e0, e1;
-        P2M_CUDA_TRY(cudaEventCreate(&e0));
-        P2M_CUDA_TRY(cudaEventCreate(&e1));
+        Event e0, e1;
+        P2M_CUDA_TRY(cudaEventCreate(&e0.e));
+        P2M_CUDA_TRY(cudaEventCreate(&e1.e));
         float best = 1e30f;
         int bt = tiles[0], bl = longs[1];
         for (int tile : tiles) {
@@ -276,17 +276,15 @@ int run_batch_query(p2m_index* h, const float* d_pts, const int64_t* h_off, floa
             for (int lr : longs) {
                 a.long_row = lr;
                 P2M_TRY(launch_batch(b, a, status, s));  // warm
-                P2M_CUDA_TRY(cudaEventRecord(e0, s));
+                P2M_CUDA_TRY(cudaEventRecord(e0.e, s));
                 for (int r = 0; r < 2; ++r) P2M_TRY(launch_batch(b, a, status, s));
-                P2M_CUDA_TRY(cudaEventRecord(e1, s));
-                P2M_CUDA_TRY(cudaEventSynchronize(e1));
+                P2M_CUDA_TRY(cudaEventRecord(e1.e, s));
+                P2M_CUDA_TRY(cudaEventSynchronize(e1.e));
                 float ms = 0;
-                P2M_CUDA_TRY(cudaEventElapsedTime(&ms, e0, e1));
+                P2M_CUDA_TRY(cudaEventElapsedTime(&ms, e0.e, e1.e));
                 if (ms < best) { best = ms; bt = tile; bl = lr; }
             }
         }
-        cudaEventDestroy(e0);
-        cudaEventDestroy(e1);
         P2M_TRY(make_tiles(b, off, bt));
         b.long_row = bl;
         b.tuned = true;

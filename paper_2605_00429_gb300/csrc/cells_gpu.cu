@@ -253,13 +253,13 @@ int SiteSet::clip_cells_gpu(const double dom_lo[3], const double dom_hi[3], doub
         return -2;
     const double tol = clip_tol(diag);
     const int blocks = std::max(1, std::min((n + 63) / 64, 152 * 16));
-    cudaEvent_t e0 = nullptr, e1 = nullptr;
-    if (cudaEventCreate(&e0) || cudaEventCreate(&e1) || cudaEventRecord(e0, s)) return -2;
+    Event e0, e1;
+    if (cudaEventCreate(&e0.e) || cudaEventCreate(&e1.e) || cudaEventRecord(e0.e, s)) return -2;
     k_clip_cells<<<blocks, 64, 0, s>>>(d_site.as<double>(), n, d_off.as<int64_t>(), d_nb.as<int32_t>(),
                                        make_double3(dom_lo[0], dom_lo[1], dom_lo[2]),
                                        make_double3(dom_hi[0], dom_hi[1], dom_hi[2]), tol, kMaxClip,
                                        d_slab.as<double>(), d_count.as<int>(), d_state.as<int>());
-    if (cudaGetLastError() != cudaSuccess || cudaEventRecord(e1, s)) return -2;
+    if (cudaGetLastError() != cudaSuccess || cudaEventRecord(e1.e, s)) return -2;
     // meanwhile, the host clips the cells the kernel hands over at once (more neighbours
     // than the device polytope has planes for)
     const auto th0 = std::chrono::steady_clock::now();
@@ -276,9 +276,7 @@ int SiteSet::clip_cells_gpu(const double dom_lo[3], const double dom_hi[3], doub
         cudaStreamSynchronize(s))
         return -2;
     float kms = 0.f;
-    cudaEventElapsedTime(&kms, e0, e1);
-    cudaEventDestroy(e0);
-    cudaEventDestroy(e1);
+    cudaEventElapsedTime(&kms, e0.e, e1.e);
     if (ms_kernel) *ms_kernel = kms;
     // the few cells that overflowed the device polytope or met a degenerate cut
     const auto th1 = std::chrono::steady_clock::now();

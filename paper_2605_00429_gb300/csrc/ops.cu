@@ -274,11 +274,10 @@ int p2m_query_host(p2m_index* h, const float* h_pts, int64_t n, float* h_dist, f
     for (auto& st : h->streams)
         if (!st) P2M_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
     // the pipeline starts after the caller's earlier work on `stream`
-    cudaEvent_t ev;
-    P2M_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
-    P2M_CUDA_TRY(cudaEventRecord(ev, user));
-    for (auto& st : h->streams) P2M_CUDA_TRY(cudaStreamWaitEvent(st, ev, 0));
-    cudaEventDestroy(ev);
+    Event ev;
+    P2M_CUDA_TRY(cudaEventCreateWithFlags(&ev.e, cudaEventDisableTiming));
+    P2M_CUDA_TRY(cudaEventRecord(ev.e, user));
+    for (auto& st : h->streams) P2M_CUDA_TRY(cudaStreamWaitEvent(st, ev.e, 0));
     // Chunks of ~n/k (at least 1M points) on kSlots streams: while one chunk computes, the
     // copy engines move the previous chunk's results out and the next chunk's points in.
     // Two chunks by default: a chunk's Morton order only groups its own points, so smaller

@@ -58,6 +58,15 @@ struct DevBuf {
     template <class T> T* as() const { return static_cast<T*>(p); }
 };
 
+// Owns a CUDA event: destroyed when it goes out of scope, early error returns included.
+struct Event {
+    cudaEvent_t e = nullptr;
+    Event() = default;
+    Event(const Event&) = delete;
+    Event& operator=(const Event&) = delete;
+    ~Event() { if (e) cudaEventDestroy(e); }
+};
+
 // ----------------------------------------------------------------------------- BVH
 
 // Binary BVH node holding the boxes of both children (one 64-byte load tests both).
