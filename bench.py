@@ -410,7 +410,8 @@ def main():
         t = time.perf_counter()
         for _ in range(e2e_steps):
             idx.query_host(hp, hd, hc, ht, hb)
-        e2e_s = (time.perf_counter() - t) / e2e_steps
+        # every leg below is whole-job: N ranks' queries over the slowest rank's time
+        e2e_s = reduce_max_ms((time.perf_counter() - t) / e2e_steps * 1e3, world, dev) / 1e3
         line["e2e"] = {"value": world * n / e2e_s, "unit": "queries/s", "h2d_bytes_per_step": 12 * n,
                        "d2h_bytes_per_step": 32 * n}
         # fwd + bwd on the differentiation workload
@@ -436,8 +437,8 @@ def main():
             fb()
         e1.record()
         torch.cuda.synchronize()
-        fb_ms = e0.elapsed_time(e1) / fsteps
-        line["fwd_bwd"] = {"value": dq.shape[0] / (fb_ms / 1e3), "unit": "queries/s", "ms_per_step": fb_ms,
+        fb_ms = reduce_max_ms(e0.elapsed_time(e1) / fsteps, world, dev)
+        line["fwd_bwd"] = {"value": world * dq.shape[0] / (fb_ms / 1e3), "unit": "queries/s", "ms_per_step": fb_ms,
                            "workload": WORKLOADS["diff"][0] + "; loss = sum d^2, grads to points and vertices"}
         # batching: 256 meshes behind one persistent launch (graph) vs one launch per mesh
         meshes, bq = W.workload_batch(256)
@@ -460,9 +461,10 @@ def main():
                 bidx.batch_query(bpts, boff, mode=mode, use_graph=graph, out=bout)
             e1.record()
             torch.cuda.synchronize()
-            res[label] = e0.elapsed_time(e1) / bsteps
-        line["batch"] = {"value": nb / (res["batched"] / 1e3), "unit": "queries/s", "ms_per_step": res["batched"],
-                         "per_mesh_value": nb / (res["per_mesh"] / 1e3), "per_mesh_ms": res["per_mesh"],
+            res[label] = reduce_max_ms(e0.elapsed_time(e1) / bsteps, world, dev)
+        line["batch"] = {"value": world * nb / (res["batched"] / 1e3), "unit": "queries/s",
+                         "ms_per_step": res["batched"],
+                         "per_mesh_value": world * nb / (res["per_mesh"] / 1e3), "per_mesh_ms": res["per_mesh"],
                          "speedup": res["per_mesh"] / res["batched"], "queries": nb, "meshes": len(meshes),
                          "tris": int(sum(m_.n_tris for m_ in meshes)),
                          "workload": "256 noisy geodesic spheres / capped cylinders, T log-uniform [500, 200k], "
