@@ -4,8 +4,11 @@
 // queries; a persistent grid (SM count x resident blocks) pulls tiles from an atomic queue
 // and answers each query exactly as the single-mesh path does (nearest site, list scan).
 // Queries whose list is longer than `long_row` are queued for a persistent warp-per-query
-// pass, and the few points outside their mesh's domain box take the BVH search.  The whole
-// sequence (counter reset + three kernels) is captured once in a CUDA graph and replayed.
+// pass, and the few points outside their mesh's domain box take the BVH search.  Before
+// that, every mesh's queries are radix-sorted by (mesh, Morton code of their grid cell) and
+// gathered into sort order; results leave as 32-byte records split into the outputs.  The
+// whole sequence (counter reset, sort, gather, thread and warp passes, split, BVH pass) is
+// captured once in a CUDA graph and replayed.
 // An autotuner picks (tile, long_row) by timing the candidates on the caller's own batch.
 #include <algorithm>
 #include <cstring>

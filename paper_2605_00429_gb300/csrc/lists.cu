@@ -272,7 +272,9 @@ __global__ void k_i64_to_i32(const int64_t* __restrict__ a, int32_t* __restrict_
         b[i] = (int32_t)a[i];
 }
 
-// Builds m.d_row_off / m.d_row_tri from the device ball table (d_balls, d_ball_off).
+// Builds the lists from the device ball table (d_balls, d_ball_off): m.d_row_off, the
+// (triangle, key) entries m.d_row_ent (short lists sorted by key), the chunk boxes and the
+// level-1 boxes.
 // List entries as (triangle, key bits) pairs: the thread scan reads both with one 8-byte load.
 __global__ void k_pack_entries(const int32_t* __restrict__ row_tri, const float* __restrict__ row_key, int64_t nnz,
                                int2* __restrict__ row_ent) {
