@@ -31,7 +31,6 @@ sys.path.insert(0, ROOT)
 import p2m_workloads as W  # noqa: E402
 
 PEAKS_FILE = os.path.join(ROOT, "MEASURED_PEAKS.json")
-SM_COUNT = 152
 FP32_LANES_PER_SM = 128
 # algorithmic FP32 work model (FLOP, an FMA counts 2): a candidate site is a squared
 # distance and a compare, a list entry the bounding-sphere test, an exact test the weighted
@@ -139,7 +138,9 @@ class ClockSampler:
 # memsets not counted).  Sorted schedules 0 and 4: k_cell_rank, k_cell_scatter, the scan
 # kernel(s) (k_query_thread, or k_query_sites + k_query_scan), k_query_warp, k_split_records,
 # k_bvh_closest.  Schedules 1-3 (unsorted): k_query_thread, k_query_warp, k_bvh_closest.
-OWN_KERNELS_PER_STEP = {0: 6, 1: 3, 2: 3, 3: 3, 4: 7}
+# Schedule 5 (site-staged): k_site_rank, k_site_scatter, k_query_staged, k_query_warp,
+# k_split_records, k_bvh_closest.
+OWN_KERNELS_PER_STEP = {0: 6, 1: 3, 2: 3, 3: 3, 4: 7, 5: 6}
 
 
 def query_source_hash():
@@ -299,6 +300,9 @@ def main():
     ap.add_argument("--no-extras", action="store_true", help="skip fwd+bwd and e2e legs")
     ap.add_argument("--schedule", type=int, default=0)
     ap.add_argument("--ablation", action="store_true", help="Table-4 style runs with / without site augmentation")
+    ap.add_argument("--profile-range", action="store_true",
+                    help="after the warm-up, run one query pass between cudaProfilerStart/Stop and exit "
+                         "(for ncu --profile-from-start off)")
     args = ap.parse_args()
     if args.ablation:
         return run_ablation(args)
@@ -343,6 +347,13 @@ def main():
     for _ in range(args.warmup):
         idx.query(pts, out=out)
     torch.cuda.synchronize()
+    if args.profile_range:
+        torch.cuda.profiler.start()
+        idx.query(pts, out=out)
+        torch.cuda.synchronize()
+        torch.cuda.profiler.stop()
+        print(json.dumps({"profile_range": desc, "queries": n, "schedule": args.schedule}), flush=True)
+        return
 
     # instrumented pass (untimed): work counters for the algorithmic FLOP count
     cnt = idx.counters(pts)
@@ -368,7 +379,8 @@ def main():
 
     pk, pk_kind = peaks()
     sm_max = float(pk.get("sm_max_mhz", 2070.0))
-    alu_peak = SM_COUNT * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
+    sm_count = torch.cuda.get_device_properties(dev).multi_processor_count
+    alu_peak = sm_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
     flops = (FLOP_PER_SITE * cnt["site_candidates"] + FLOP_PER_ROW_ENTRY * cnt["row_entries"] +
              FLOP_PER_EXACT * cnt["exact_tests"] + FLOP_PER_QUERY * n)
     achieved = flops / (ms / 1e3) / 1e12
@@ -384,7 +396,9 @@ def main():
                          "frac": achieved / alu_peak, "traffic": profiled_traffic(args.config, n),
                          "l1tex_pct_ncu": profiled_l1tex_pct(args.config),
                          "kernel": "k_query_thread + k_query_warp (one query pass)",
-                         "peak_kind": f"FP32 FMA lanes x max SM clock from {pk_kind} peaks",
+                         "peak_kind": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x max SM clock "
+                                      f"from {pk_kind} peaks",
+                         "sm_count": sm_count,
                          "hbm_achieved_gbs": hbm_gbs, "hbm_peak_gbs": pk.get("hbm_gbs"),
                          "hbm_frac": hbm_gbs / float(pk.get("hbm_gbs", 6800.0))},
             "clocks": {k: clocks[k] for k in ("sm_mhz", "sm_max_mhz", "reasons")},

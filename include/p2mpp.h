@@ -8,7 +8,8 @@
  *   * Each site's cell is a convex polytope; its interception list is every triangle that
  *     meets the union of balls B(u, ||u - v||) centred at the cell's corners u, with v the
  *     site's reference point on the mesh (Section 3.3, Eq. 2, Eq. 3 "Vertex Sphere Union").
- *     An off-surface site uses one ball of radius Eq. 8 around itself instead.
+ *     An off-surface site uses v = proj(s, M): its corner balls, or (aux_balls = 0) the one
+ *     ball of radius Eq. 8 around itself that encloses them.
  *   * A query finds its nearest site and scans only that site's list, pruning with each
  *     triangle's bounding sphere (Section 3.3 "Distance Query Stage", "Bounding Sphere
  *     Pruning").  The result is the exact closest point on the mesh.
@@ -25,7 +26,14 @@
  *   * Points and vertices are float32 xyz triples, row-major [n,3].  Triangle ids index
  *     the caller's `tris` array; barycentrics (b0,b1,b2) refer to that triangle's
  *     (v0,v1,v2) so that closest = b0 v0 + b1 v1 + b2 v2.
- *   * Sizes are int64_t.  n == 0 is a successful no-op wherever n appears.
+ *   * Sizes are int64_t.  n == 0 is a successful no-op wherever n appears.  A call takes at
+ *     most 2^31 - 1 points (larger n returns P2M_ERR_LIMIT: split the call).
+ *   * The device an index was built on must be current when it is used (else
+ *     P2M_ERR_INVALID_ARG): its buffers, and the scratch it reuses, live there.
+ *   * Calls on one index share its scratch buffers (sort keys, queues, result records, the
+ *     host pipeline's staging buffers).  Issue them on one stream, or order them with events:
+ *     two calls on the same index whose work overlaps on the GPU race on that scratch.
+ *     Different indexes are independent.
  */
 #ifndef P2MPP_H
 #define P2MPP_H
@@ -77,8 +85,10 @@ typedef struct {
      * thread per query for lists up to long_list entries and a warp-cooperative best-first
      * scan for longer lists; 1 = thread per query for every list; 2 = warp per query for
      * every list; 3 = as 0 without the sort; 4 = as 0, with the queries regrouped by
-     * nearest site (a second radix sort) before the list scan.  All give identical
-     * results. */
+     * nearest site (a second radix sort) before the list scan; 5 = queries counting-sorted
+     * by nearest site, each block of 256 staging its runs' short lists (entries, spheres,
+     * triangle records, chunk boxes) in shared memory before the scan, long lists as in 0.
+     * All give identical results. */
     int schedule;
     /* Deterministic vertex-gradient accumulation (fixed-point integer atomics) [1]. */
     int deterministic;
@@ -94,6 +104,12 @@ typedef struct {
      * More chunks overlap copies and compute better; fewer keep more queries per grid cell
      * in each chunk's Morton order. */
     int pipe_chunks;
+    /* Balls of an auxiliary (off-surface) site [1]: 1 = one ball per corner u of its cell with
+     * radius ||u - proj(s, M)|| (Eq. 3 with the reference point proj(s, M), merged to at most 128
+     * like a vertex site's); 0 = the single enclosing ball of Eq. 8 around s.  Eq. 8's ball
+     * contains the corner balls (triangle inequality), so both give exact results; the corner
+     * balls give shorter lists where the cell is large. */
+    int aux_balls;
 } p2m_build_params;
 
 /* Build statistics (Section 4.1, Table 1: Max / Avg list length) and stage timings. */
@@ -225,8 +241,11 @@ int p2m_query_counters(p2m_index* h, const float* d_pts, int64_t n, float* d_dis
  * p is recomputed from the index's current vertices and d_tri / d_bary of the forward.
  * d_grad_pts may be NULL; d_grad_verts may be NULL; d_grad_verts[n_verts*3] is
  * ACCUMULATED into (zero it first).  With params.deterministic the vertex sums are
- * bit-reproducible (fixed-point integer atomics).  Asynchronous.  Errors: INVALID_ARG,
- * OOM, CUDA. */
+ * bit-reproducible: fixed-point integer atomics whose unit 2^-e is picked per call from
+ * B = max_i |g_i| max(1, max_k |b_ik|) so that 3 n B 2^e <= 2^62 (no sum can overflow; each
+ * contribution is rounded to the unit, an error of at most 3 n B 2^-63).  There a non-finite
+ * g or b leaves d_grad_pts and d_grad_verts untouched and makes the next synchronising call
+ * on the index return P2M_ERR_LIMIT.  Asynchronous.  Errors: INVALID_ARG, OOM, CUDA. */
 int p2m_backward(p2m_index* h, const float* d_pts, int64_t n, const int32_t* d_tri,
                  const float* d_bary, const float* d_grad_dist, float* d_grad_pts,
                  float* d_grad_verts, void* stream);
@@ -274,7 +293,16 @@ int p2m_get_sites(const p2m_index* h, int mesh, float* h_sites, double* h_ref, i
 /* Interception lists (CSR) of mesh `mesh`: h_offsets[n_sites+1], h_tri_ids[nnz]. */
 int p2m_get_lists(const p2m_index* h, int mesh, int64_t* h_offsets, int32_t* h_tri_ids);
 
-/* Corner balls of mesh `mesh` (Eq. 3 / Eq. 8): h_ball_offsets[n_sites+1] into
+/* Triangle BVH of mesh `mesh` (the LBVH of Section 3.3 "Implementation Details" that the
+ * corner balls are tested against, and the exact search for points outside D uses).
+ * *n_nodes = n_tris - 1 internal nodes (0 for a one-triangle mesh); *root = the root node, or
+ * ~0 when the only node is a leaf.  h_nodes[n_nodes*16] float32, per node: the box of child 0
+ * (lo.xyz, child ref, hi.xyz, 0) then the box of child 1 (same layout); a child ref is int32
+ * bits, >= 0 an internal node, < 0 a leaf ~k where k is a leaf position.  h_leaf_tri[n_tris]
+ * = the caller's triangle id stored at each leaf position.  Either pointer may be NULL. */
+int p2m_get_bvh(const p2m_index* h, int mesh, int64_t* n_nodes, int32_t* root, float* h_nodes, int32_t* h_leaf_tri);
+
+/* Corner balls of mesh `mesh` (Eq. 3, or Eq. 8 for auxiliary sites with aux_balls = 0): h_ball_offsets[n_sites+1] into
  * h_centres[n_balls*3] (float64) and h_radii[n_balls] (float64, before slack). */
 int p2m_get_balls(const p2m_index* h, int mesh, int64_t* h_ball_offsets, double* h_centres,
                   double* h_radii);

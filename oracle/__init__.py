@@ -11,6 +11,8 @@ Contents (each a plain, slow definition; see ``oracle.c`` for the C part):
 * ``nearest_site``  brute-force FP64 nearest site (cell locate, Section 3.3).
 * ``ball_margin``   per triangle, min over balls of d(u, f) - r_u (Eq. 3, Eq. 8).
 * ``aux_radius``    Eq. 8 for an off-surface site.
+* ``voronoi_cell``  corners of one site's Voronoi cell clipped to the domain box, from the
+                    bisectors of every other site (no neighbour search).
 * ``winding``       generalized winding number (inside / outside of a closed mesh), the
                     plain definition behind the sign of the signed distance.
 * ``grad_analytic`` gradient of sum_i g_i d(q_i, M) w.r.t. queries and vertices, from the
@@ -135,6 +137,30 @@ def signed_distance(verts, tris, pts, res=None):
         res = closest(verts, tris, pts)
     w = winding(verts, tris, pts)
     return np.where(w > 0.5, -res["dist"], res["dist"]), w
+
+
+def voronoi_cell(sites, i, dom_lo, dom_hi):
+    """Corners of the Voronoi cell of site i clipped to the box D = [dom_lo, dom_hi], in FP64.
+
+    The cell is the plain definition {x in D : ||x - s_i|| <= ||x - s_j|| for every j != i}
+    (Section 3.1: each site owns the points nearer to it than to any other site).  Squaring
+    both sides, each other site gives the half-space 2 x.(s_j - s_i) <= |s_j|^2 - |s_i|^2;
+    all of them are used, with the six faces of D.  The vertices of that intersection of
+    half-spaces come from Qhull (scipy.spatial.HalfspaceIntersection), a library step, started
+    from the interior point s_i.  A vertex where more than three planes meet may be listed more
+    than once.  Needs distinct sites and s_i strictly inside D."""
+    from scipy.spatial import HalfspaceIntersection
+    S = np.asarray(sites, dtype=np.float64).reshape(-1, 3)
+    lo = np.asarray(dom_lo, dtype=np.float64).reshape(3)
+    hi = np.asarray(dom_hi, dtype=np.float64).reshape(3)
+    s = S[i]
+    other = np.delete(S, i, axis=0)
+    # rows (a, b) of a.x + b <= 0
+    bis = np.c_[2.0 * (other - s), -(np.sum(other * other, axis=1) - np.dot(s, s))]
+    box = np.array([[-1, 0, 0, lo[0]], [0, -1, 0, lo[1]], [0, 0, -1, lo[2]],
+                    [1, 0, 0, -hi[0]], [0, 1, 0, -hi[1]], [0, 0, 1, -hi[2]]], dtype=np.float64)
+    hs = HalfspaceIntersection(np.vstack([bis, box]), s)
+    return np.asarray(hs.intersections, dtype=np.float64)
 
 
 def aux_radius(site, corners, proj):

@@ -31,7 +31,7 @@ class BuildParams(ctypes.Structure):
                 ("ring_radius_scale", ctypes.c_float), ("build_eps_rel", ctypes.c_float),
                 ("nn_grid_res", ctypes.c_int), ("schedule", ctypes.c_int), ("deterministic", ctypes.c_int),
                 ("seed", ctypes.c_int), ("long_list", ctypes.c_int), ("gpu_cells", ctypes.c_int),
-                ("pipe_chunks", ctypes.c_int)]
+                ("pipe_chunks", ctypes.c_int), ("aux_balls", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):
@@ -84,6 +84,7 @@ SIGNATURES = {
     "p2m_get_sites": ([_P, _I, _P, _P, _P], _I),
     "p2m_get_lists": ([_P, _I, _P, _P], _I),
     "p2m_get_balls": ([_P, _I, _P, _P, _P], _I),
+    "p2m_get_bvh": ([_P, _I, _P, _P, _P, _P], _I),
     "p2m_voronoi_cells": ([_P, _I64, _P, _P, _I, _P, _P, _P, _P], _I),
     "p2m_voronoi_cells_device": ([_P, _I64, _P, _P, _I, _P, _P, _P, _P, _P, _P], _I),
     "p2m_query_noalloc": ([_P, _P, _I64, _P, _P, _P, _P, _P], _I),
@@ -162,6 +163,10 @@ class P2MIndex:
         p = default_params(**params)
         _check(lib().p2m_build(v.ctypes.data_as(_P), v.shape[0], t.ctypes.data_as(_P), t.shape[0], 0,
                                ctypes.byref(p), _stream_ptr(), ctypes.byref(self._h)))
+        # the vertices the index was built on (checked by unsigned_distance)
+        self._verts = v.copy()
+        self._verts_dev = None
+        self._vtoken = None
 
     @classmethod
     def batch(cls, meshes, **params):
@@ -276,8 +281,29 @@ class P2MIndex:
                                   _dptr(grad_pts), _dptr(grad_verts), _stream_ptr(stream)))
 
     def update_vertices(self, verts, stream=None):
-        verts = verts.contiguous()
+        src = verts
+        verts = verts.detach().contiguous()
         _check(lib().p2m_update_vertices(self._h, _dptr(verts), _stream_ptr(stream)))
+        self._verts_dev = verts.float().clone()
+        self._verts = None
+        self._vtoken = (src.data_ptr(), src._version, tuple(src.shape))
+
+    def check_vertices(self, verts):
+        """Raise if `verts` differ from the vertices this index was built on (or last updated
+        to).  A tensor seen before and not modified in place since is accepted without a
+        comparison; anything else is compared element by element once."""
+        import torch
+        token = (verts.data_ptr(), verts._version, tuple(verts.shape))
+        if token == getattr(self, "_vtoken", None):
+            return
+        if getattr(self, "_verts_dev", None) is None or self._verts_dev.device != verts.device:
+            base = self._verts if self._verts is not None else self._verts_dev.cpu().numpy()
+            self._verts_dev = torch.from_numpy(np.ascontiguousarray(base)).to(verts.device)
+        if tuple(verts.shape) != tuple(self._verts_dev.shape) or \
+                not torch.equal(verts.detach().to(torch.float32), self._verts_dev):
+            raise ValueError("the vertices differ from the ones the index was built on: call "
+                             "index.update_vertices(verts) after moving them, or the gradients would be stale")
+        self._vtoken = token
 
     def batch_query(self, pts, offsets, mode=0, use_graph=True, out=None, stream=None):
         """pts: CUDA [N,3] (queries of mesh i at offsets[i]:offsets[i+1]); returns CUDA outputs."""
@@ -319,6 +345,18 @@ class P2MIndex:
         ids = np.empty(max(nnz, 1), np.int32)
         _check(lib().p2m_get_lists(self._h, mesh, off.ctypes.data_as(_P), ids.ctypes.data_as(_P)))
         return off, ids[:nnz]
+
+    def bvh(self, mesh=0):
+        """(root, nodes [n_nodes,16] float32 as stored, leaf_tri [n_tris] int32)."""
+        nn, root = ctypes.c_int64(), ctypes.c_int32()
+        _check(lib().p2m_get_bvh(self._h, mesh, ctypes.byref(nn), ctypes.byref(root), None, None))
+        nodes = np.empty((max(nn.value, 1), 16), np.float32)
+        n_tris = self.stats()["n_tris"] if getattr(self, "n_meshes", 1) == 1 else None
+        if n_tris is None:
+            raise ValueError("bvh() of a batch index: use the single-mesh index")
+        leaf = np.empty(n_tris, np.int32)
+        _check(lib().p2m_get_bvh(self._h, mesh, None, None, nodes.ctypes.data_as(_P), leaf.ctypes.data_as(_P)))
+        return root.value, nodes[:nn.value], leaf
 
     def balls(self, mesh=0):
         S, _, B = self.sizes(mesh)
@@ -376,10 +414,12 @@ def _make_function():
         """d(q, M) for query points q with gradients w.r.t. q and the mesh vertices.
 
         forward(pts [n,3], verts [V,3], index) -> dist [n].  The index must have been built
-        on `verts` (rebuild or call ``index.update_vertices`` when they change)."""
+        on `verts` (rebuild or call ``index.update_vertices`` when they change); other
+        vertices raise ValueError instead of giving stale gradients."""
 
         @staticmethod
         def forward(ctx, pts, verts, index):
+            index.check_vertices(verts)
             dist, _, tri, bary = index.query(pts, want_closest=False)
             ctx.save_for_backward(pts, tri, bary)
             ctx.index = index

@@ -145,11 +145,9 @@ __global__ void k_batch_keys(BatchArgs a, unsigned long long* __restrict__ key, 
 }
 
 static int persistent_blocks(const void* kernel, int threads) {
-    int per_sm = 1, dev = 0, sms = 152;
-    cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    int per_sm = 1;
     cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, threads, 0);
-    return std::max(1, per_sm) * sms;
+    return std::max(1, per_sm) * sm_count();
 }
 
 // The launch sequence of one batched query (captured into the graph when requested).
@@ -161,7 +159,7 @@ static int launch_batch(BatchState& b, const BatchArgs& a0, unsigned* status, cu
         const int64_t N = b.offsets.back();
         unsigned long long* k0 = b.sort_keys.as<unsigned long long>();
         int32_t* i0 = b.sort_idx.as<int32_t>();
-        k_batch_keys<<<std::max(1, std::min(a.n_tiles, 152 * 32)), 256, 0, s>>>(a, k0, i0);
+        k_batch_keys<<<std::max(1, std::min(a.n_tiles, sm_count() * 32)), 256, 0, s>>>(a, k0, i0);
         P2M_CUDA_TRY(cudaGetLastError());
         cub::DoubleBuffer<unsigned long long> dk(k0, k0 + N);
         cub::DoubleBuffer<int32_t> dv(i0, i0 + N);

@@ -259,7 +259,7 @@ int gather_f4(DevBuf& buf, const int* d_order, int n, int per, cudaStream_t s) {
     DevBuf out;
     P2M_TRY(out.alloc(sizeof(float4) * (size_t)n * per));
     const int64_t tot = (int64_t)n * per;
-    k_gather_f4<<<(int)std::min<int64_t>((tot + 255) / 256, 152 * 64), 256, 0, s>>>(buf.as<float4>(), out.as<float4>(),
+    k_gather_f4<<<(int)std::min<int64_t>((tot + 255) / 256, sm_count() * 64), 256, 0, s>>>(buf.as<float4>(), out.as<float4>(),
                                                                                    d_order, n, per);
     P2M_CUDA_TRY(cudaGetLastError());
     P2M_CUDA_TRY(cudaStreamSynchronize(s));
@@ -301,7 +301,7 @@ int launch_bvh_closest(const MeshView& m, const float* d_pts, const int32_t* d_i
     // with a device-side count the launch is sized for a modest share of n: the grid-stride
     // loop covers the rest
     const int64_t want = (n + bs - 1) / bs;
-    const int64_t blocks = d_count ? std::min<int64_t>(want, 152 * 8) : std::min<int64_t>(want, 152 * 64);
+    const int64_t blocks = d_count ? std::min<int64_t>(want, sm_count() * 8) : std::min<int64_t>(want, sm_count() * 64);
     k_bvh_closest<<<(unsigned)std::max<int64_t>(blocks, 1), bs, 0, s>>>(m.bvh, m.bvh_root, m.tri, d_pts, d_idx, d_count,
                                                                          n, d_dist, d_closest, d_tri, d_bary, d_status,
                                                                          m.orig);

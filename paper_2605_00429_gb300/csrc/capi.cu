@@ -42,6 +42,23 @@ static bool inject_alloc_fault() {
     return ++count == std::atol(v.c_str() + 6);
 }
 
+int sm_count() {
+    static std::atomic<int> cache[64];
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) {
+        cudaGetLastError();
+        return 148;
+    }
+    int v = cache[dev].load(std::memory_order_relaxed);
+    if (v > 0) return v;
+    if (cudaDeviceGetAttribute(&v, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess || v <= 0) {
+        cudaGetLastError();
+        return 148;
+    }
+    cache[dev].store(v, std::memory_order_relaxed);
+    return v;
+}
+
 bool inject_fault(const char* what) {
     const char* e = std::getenv("P2M_FAULT");
     return e && std::strcmp(e, what) == 0;
@@ -124,6 +141,18 @@ int check_status_word(p2m_index* h, cudaStream_t s, const char* what) {
     return P2M_OK;
 }
 
+int check_call(const p2m_index* h, int64_t n, const char* what) {
+    int dev = -1;
+    P2M_CUDA_TRY(cudaGetDevice(&dev));
+    if (dev != h->device)
+        return fail(P2M_ERR_INVALID_ARG, std::string(what) + ": the index was built on device " + std::to_string(h->device) +
+                                             " but device " + std::to_string(dev) + " is current");
+    if (n > 0x7fffffffLL)
+        return fail(P2M_ERR_LIMIT, std::string(what) + ": " + std::to_string(n) +
+                                       " points in one call (at most 2^31 - 1); split the call");
+    return P2M_OK;
+}
+
 }  // namespace p2m
 
 p2m_index::~p2m_index() {
@@ -140,10 +169,11 @@ static int validate_params(const p2m_build_params& p) {
     if (p.ring_sites != 6 && p.ring_sites != 12) return fail(P2M_ERR_INVALID_ARG, "ring_sites must be 6 or 12");
     if (!(p.ring_radius_scale > 0.0f)) return fail(P2M_ERR_INVALID_ARG, "ring_radius_scale must be > 0");
     if (!(p.build_eps_rel >= 0.0f && p.build_eps_rel < 1e-2f)) return fail(P2M_ERR_INVALID_ARG, "build_eps_rel out of range");
-    if (p.nn_grid_res < 0 || p.nn_grid_res > 1024) return fail(P2M_ERR_INVALID_ARG, "nn_grid_res out of range");
-    if (p.schedule < 0 || p.schedule > 4) return fail(P2M_ERR_INVALID_ARG, "schedule must be 0..4");
+    if (p.nn_grid_res < 0 || p.nn_grid_res > 1023) return fail(P2M_ERR_INVALID_ARG, "nn_grid_res out of range");
+    if (p.schedule < 0 || p.schedule > 5) return fail(P2M_ERR_INVALID_ARG, "schedule must be 0..5");
     if (p.long_list < 0) return fail(P2M_ERR_INVALID_ARG, "long_list must be >= 0");
     if (p.pipe_chunks < 0) return fail(P2M_ERR_INVALID_ARG, "pipe_chunks must be >= 0");
+    if (p.aux_balls != 0 && p.aux_balls != 1) return fail(P2M_ERR_INVALID_ARG, "aux_balls must be 0 or 1");
     return P2M_OK;
 }
 
@@ -308,6 +338,7 @@ static int build_mesh(MeshData& m, const p2m_build_params& prm, p2m_index* h, cu
     m.long_row = prm.schedule == 1 ? 0x7fffffff : (prm.schedule == 2 ? 0 : long_list);
     m.sorted = prm.schedule == 0 || prm.schedule == 4;
     m.site_sorted = prm.schedule == 4;
+    m.site_staged = prm.schedule == 5;
     // host Voronoi, augmentation, corner balls, lists, nearest-site grid
     P2M_TRY(build_partition(m, prm, h, s));
     st.ms_total = now_ms() - t0;
@@ -336,6 +367,7 @@ int p2m_default_params(p2m_build_params* out) {
     out->deterministic = 1;
     out->seed = 1;
     out->gpu_cells = 1;
+    out->aux_balls = 1;
     return P2M_OK;
 }
 
@@ -378,6 +410,7 @@ int p2m_query(p2m_index* h, const float* d_pts, int64_t n, float* d_dist, float*
     if (n < 0) return fail(P2M_ERR_INVALID_ARG, "n < 0");
     if (n == 0) return P2M_OK;
     if (!d_pts || !d_dist) return fail(P2M_ERR_INVALID_ARG, "d_pts and d_dist must be non-NULL");
+    P2M_TRY(check_call(h, n, "p2m_query"));
     return run_query(h, *h->meshes[0], d_pts, n, d_dist, d_closest, d_tri, d_bary, nullptr, h->scratch_idx,
                      (cudaStream_t)stream);
 }
@@ -388,6 +421,7 @@ int p2m_query_counters(p2m_index* h, const float* d_pts, int64_t n, float* d_dis
     if (n < 0 || (n > 0 && !d_pts)) return fail(P2M_ERR_INVALID_ARG, "bad points");
     std::memset(out, 0, sizeof(*out));
     if (n == 0) return P2M_OK;
+    P2M_TRY(check_call(h, n, "p2m_query_counters"));
     cudaStream_t s = (cudaStream_t)stream;
     DevBuf cnt, dist;
     P2M_TRY(cnt.alloc(sizeof(unsigned long long) * 8));
@@ -416,6 +450,7 @@ int p2m_nearest_site(p2m_index* h, const float* d_pts, int64_t n, int32_t* d_sit
     if (!h || h->meshes.size() != 1) return fail(P2M_ERR_INVALID_ARG, "p2m_nearest_site needs a single-mesh index");
     if (n < 0 || (n > 0 && (!d_pts || !d_site))) return fail(P2M_ERR_INVALID_ARG, "bad arguments");
     if (n == 0) return P2M_OK;
+    P2M_TRY(check_call(h, n, "p2m_nearest_site"));
     return run_nearest_site(h, *h->meshes[0], d_pts, n, d_site, (cudaStream_t)stream);
 }
 
@@ -491,6 +526,18 @@ int p2m_get_lists(const p2m_index* h, int mesh, int64_t* h_offsets, int32_t* h_t
     return P2M_OK;
 }
 
+int p2m_get_bvh(const p2m_index* h, int mesh, int64_t* n_nodes, int32_t* root, float* h_nodes, int32_t* h_leaf_tri) {
+    MeshData* m;
+    P2M_TRY(mesh_of(h, mesh, &m));
+    const int64_t nn = m->bvh.n_prims > 1 ? m->bvh.n_prims - 1 : 0;
+    if (n_nodes) *n_nodes = nn;
+    if (root) *root = m->bvh.root;
+    if (h_nodes && nn > 0)
+        P2M_CUDA_TRY(cudaMemcpy(h_nodes, m->bvh.nodes.p, sizeof(BNode) * nn, cudaMemcpyDeviceToHost));
+    if (h_leaf_tri) std::memcpy(h_leaf_tri, m->orig.data(), sizeof(int32_t) * m->orig.size());
+    return P2M_OK;
+}
+
 int p2m_get_balls(const p2m_index* h, int mesh, int64_t* h_ball_offsets, double* h_centres, double* h_radii) {
     MeshData* m;
     P2M_TRY(mesh_of(h, mesh, &m));
@@ -561,12 +608,14 @@ int p2m_batch_build(int n_meshes, const float* const* verts, const int64_t* n_ve
 int p2m_batch_query(p2m_index* batch, const float* d_pts, const int64_t* h_q_offsets, float* d_dist, float* d_closest,
                     int32_t* d_tri, float* d_bary, int mode, int use_graph, void* stream) {
     if (!batch || batch->meshes.empty() || !h_q_offsets) return fail(P2M_ERR_INVALID_ARG, "bad batch or offsets");
+    P2M_TRY(check_call(batch, 0, "p2m_batch_query"));
     return run_batch_query(batch, d_pts, h_q_offsets, d_dist, d_closest, d_tri, d_bary, mode, use_graph,
                            (cudaStream_t)stream);
 }
 
 int p2m_update_vertices(p2m_index* h, const float* d_verts, void* stream) {
     if (!h || h->meshes.size() != 1 || !d_verts) return fail(P2M_ERR_INVALID_ARG, "p2m_update_vertices needs a single-mesh index");
+    P2M_TRY(check_call(h, 0, "p2m_update_vertices"));
     cudaStream_t s = (cudaStream_t)stream;
     MeshData& old = *h->meshes[0];
     std::vector<float> v(old.n_verts * 3);

@@ -252,7 +252,7 @@ int SiteSet::clip_cells_gpu(const double dom_lo[3], const double dom_hi[3], doub
         (nnb > 0 && cudaMemcpyAsync(d_nb.p, nb_id.data(), sizeof(int32_t) * nnb, cudaMemcpyHostToDevice, s)))
         return -2;
     const double tol = clip_tol(diag);
-    const int blocks = std::max(1, std::min((n + 63) / 64, 152 * 16));
+    const int blocks = std::max(1, std::min((n + 63) / 64, sm_count() * 16));
     Event e0, e1;
     if (cudaEventCreate(&e0.e) || cudaEventCreate(&e1.e) || cudaEventRecord(e0.e, s)) return -2;
     k_clip_cells<<<blocks, 64, 0, s>>>(d_site.as<double>(), n, d_off.as<int64_t>(), d_nb.as<int32_t>(),
@@ -298,7 +298,7 @@ int SiteSet::clip_cells_gpu(const double dom_lo[3], const double dom_hi[3], doub
         if (d_corner.alloc(sizeof(double) * 3 * cell_off[n]) ||
             cudaMemcpyAsync(d_coff.p, cell_off.data(), sizeof(int64_t) * (n + 1), cudaMemcpyHostToDevice, s))
             return -2;
-        k_pack_corners<<<std::max(1, std::min(n, 152 * 32)), 128, 0, s>>>(d_slab.as<double>(), d_count.as<int>(),
+        k_pack_corners<<<std::max(1, std::min(n, sm_count() * 32)), 128, 0, s>>>(d_slab.as<double>(), d_count.as<int>(),
                                                                          d_coff.as<int64_t>(), n, d_corner.as<double>());
         if (cudaGetLastError() != cudaSuccess ||
             cudaMemcpyAsync(cell_xyz.data(), d_corner.p, sizeof(double) * cell_xyz.size(), cudaMemcpyDeviceToHost, s) ||
@@ -356,7 +356,7 @@ int bin_points_gpu(const std::vector<double>& w, const double lo[3], const doubl
         d_cnt.alloc(sizeof(int) * n) || d_runs.alloc(sizeof(int)) || d_tmp.alloc(std::max(t_sort, t_rle) + 16))
         return -1;
     if (cudaMemcpyAsync(d_w.p, w.data(), sizeof(double) * w.size(), cudaMemcpyHostToDevice, s)) return -1;
-    k_bin_keys<<<(int)std::min<int64_t>((n + 255) / 256, 152 * 16), 256, 0, s>>>(
+    k_bin_keys<<<(int)std::min<int64_t>((n + 255) / 256, sm_count() * 16), 256, 0, s>>>(
         d_w.as<double>(), n, make_double3(lo[0], lo[1], lo[2]), make_double3(hi[0], hi[1], hi[2]), tau, ncell[0],
         ncell[1], top, d_k0.as<unsigned long long>());
     if (cudaGetLastError() != cudaSuccess) return -1;

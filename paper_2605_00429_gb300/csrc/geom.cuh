@@ -57,16 +57,21 @@ __device__ __forceinline__ TriRec load_tri(const float4* __restrict__ tri, int f
 // 4e-6 |q - c|^2 (the unit normal is good to a few ulps in direction and length, so the
 // computed rho^2 is within about 1.5e-6 |q - c|^2 of the exact one).  dc2 = |q - c|^2.  A
 // triangle too thin to project onto has u = 0 and the bound falls back to the sphere's.
-__device__ __forceinline__ float tri_lower_bound2(const float4* __restrict__ tri, int f, float3 q, float4 sp,
-                                                  float dc2, float h_slack) {
-    const float4* p = tri + 4 * (int64_t)f;
-    const float4 a = __ldg(p), b = __ldg(p + 1);
+// a, b = the first half of the triangle's record.
+__device__ __forceinline__ float tri_lower_bound2_rec(float4 a, float4 b, float3 q, float4 sp, float dc2,
+                                                      float h_slack) {
     const float3 u = f3(a);
     const float h = fmaxf(fabsf(dot3(u, q - f3(b))) - h_slack, 0.0f);
     const float hc = dot3(u, q - f3(sp));
     const float rho2 = fmaf(-4e-6f, dc2, fmaf(-hc, hc, dc2));
     const float g = fmaxf(sqrtf(fmaxf(rho2, 0.0f)) - sp.w, 0.0f);
     return fmaf(g, g, h * h);
+}
+
+__device__ __forceinline__ float tri_lower_bound2(const float4* __restrict__ tri, int f, float3 q, float4 sp,
+                                                  float dc2, float h_slack) {
+    const float4* p = tri + 4 * (int64_t)f;
+    return tri_lower_bound2_rec(__ldg(p), __ldg(p + 1), q, sp, dc2, h_slack);
 }
 
 // Exact squared distance from q to the triangle; (s, t) locate the closest point

@@ -1,245 +1,293 @@
 // K2a: nearest-site grid.  The paper locates a query's cell by a nearest-neighbour search
-// over the sites (Section 3.3 "Recursive Nearest Neighbor Search"); here a uniform grid
-// over the domain box D stores, per grid cell, every site that can be the nearest site of
-// some point of that cell, so a query reads one short candidate list.
+// over the sites (Section 3.3 "Recursive Nearest Neighbor Search"); here a uniform grid over
+// the domain box D lists, per grid cell, the sites whose Voronoi cells meet that grid cell.
+// The nearest site of any point of the grid cell is among them (that point lies in its
+// nearest site's cell), so a query scans one short candidate list.
 //
-// Candidates of a grid cell with centre c and half-diagonal h: with d_nn(c) the nearest-
-// site distance, site s can win at a point x of the cell only if ||c - s|| <= d_nn(c) + 2h
-// (the triangle inequality twice).  Those sites come from a range query on a BVH of the
-// sites; each is then dropped if the whole cell is strictly closer to one of the 16 sites
-// nearest to c (a linear test over the cell's corners, with a margin so that rounding
-// never drops a true candidate).
+// The lists are built site by site, by rasterising each Voronoi cell into the grid.  A warp
+// takes one site s: starting from the grid-index box around the cell's corners, it splits
+// boxes in two along their longest side and drops a box as soon as the whole box lies
+// strictly on the far side of the bisector between s and one of its Delaunay neighbours t
+// (every point of the box nearer to t than to s, so no point of cell(s) is in it).  Boxes of
+// one grid cell that survive are emitted as candidates.  Dropping uses one plane at a time,
+// and at most the 96 nearest neighbours' planes, so a box cut off only by two planes together
+// (or by a farther neighbour) survives: the lists may hold a few extra sites, never miss one.  Each grid cell is tested grown by 1% of a cell on every side, so a
+// query that FP32 rounding bins into a neighbouring cell still finds its nearest site.
+//
+// Count pass (cells' candidate counts, atomics), scan, fill pass (atomic slots), then each
+// cell's list is sorted by site id (the order does not change any result; it makes the grid
+// deterministic) and packed as (x, y, z, id) so a query reads one contiguous run.
+#include <algorithm>
+#include <atomic>
+#include <cmath>
+#include <thread>
+
 #include <cub/device/device_scan.cuh>
+#include <cub/device/device_segmented_sort.cuh>
 
 #include "geom.cuh"
 #include "host.h"
+#include "voronoi.h"
 
 namespace p2m {
 
-constexpr int kKnn = 16;
-constexpr int kGridStack = 64;
-constexpr int kGridSlab = 16;  // candidates a cell keeps from the counting pass (~6 on average)
+constexpr int kRasterWarps = 4;     // warps per block, one site each
+constexpr int kRasterStack = 768;   // boxes per warp (a 32-wide depth-first walk needs <= 24 x 32)
+constexpr int kRasterPlanes = 96;   // bisectors per site staged in shared memory
 
-struct GridParams {
-    float3 lo;
-    float3 cell;      // cell size per axis
+struct RasterParams {
+    float3 lo;     // domain D lower corner
+    float3 h;      // grid cell size per axis
     int G;
-    float margin;     // rejection margin of the half-space filter (squared-length units)
+    float ext;     // extent E of D (largest |coordinate| or diagonal)
+    float rel;     // rounding margin of the bisector test, relative (see build_grid)
 };
 
-__device__ __forceinline__ float3 cell_centre(const GridParams& g, int ix, int iy, int iz) {
-    return make_float3(g.lo.x + (ix + 0.5f) * g.cell.x, g.lo.y + (iy + 0.5f) * g.cell.y, g.lo.z + (iz + 0.5f) * g.cell.z);
+// A box of grid indices [x0, x1] x [y0, y1] x [z0, z1] (inclusive, 10 bits each).
+__device__ __forceinline__ unsigned long long pack_box(int x0, int x1, int y0, int y1, int z0, int z1) {
+    return (unsigned long long)x0 | ((unsigned long long)x1 << 10) | ((unsigned long long)y0 << 20) |
+           ((unsigned long long)y1 << 30) | ((unsigned long long)z0 << 40) | ((unsigned long long)z1 << 50);
 }
 
-// k nearest sites of c by branch and bound (sorted ascending by (d2, id)).
-__device__ void knn(float3 c, const BNode* __restrict__ nodes, int root, const float4* __restrict__ sites,
-                    float* kd, int* ki, unsigned* status) {
-    for (int j = 0; j < kKnn; ++j) { kd[j] = INFINITY; ki[j] = -1; }
-    auto offer = [&](int s) {
-        const float4 p = __ldg(sites + s);
-        const float dx = p.x - c.x, dy = p.y - c.y, dz = p.z - c.z;
-        const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-        if (d2 > kd[kKnn - 1] || (d2 == kd[kKnn - 1] && s > ki[kKnn - 1])) return;
-        int j = kKnn - 1;
-        while (j > 0 && (kd[j - 1] > d2 || (kd[j - 1] == d2 && ki[j - 1] > s))) {
-            kd[j] = kd[j - 1];
-            ki[j] = ki[j - 1];
-            --j;
-        }
-        kd[j] = d2;
-        ki[j] = s;
-    };
-    if (root < 0) { offer(~root); return; }
-    int stk[kGridStack];
-    float sd[kGridStack];
-    int sp = 0, node = root;
-    while (true) {
-        const float4* np = reinterpret_cast<const float4*>(nodes + node);
-        const float4 lo0 = __ldg(np), hi0 = __ldg(np + 1), lo1 = __ldg(np + 2), hi1 = __ldg(np + 3);
-        const int cs[2] = {__float_as_int(lo0.w), __float_as_int(lo1.w)};
-        const float ds[2] = {box_dist2(c, f3(lo0), f3(hi0)), box_dist2(c, f3(lo1), f3(hi1))};
-        const int first = ds[1] < ds[0] ? 1 : 0;
-        int next = -1;
-        for (int h = 0; h < 2; ++h) {
-            const int k = h == 0 ? first : 1 - first;
-            if (ds[k] > kd[kKnn - 1]) continue;
-            if (cs[k] < 0) offer(~cs[k]);
-            else if (next < 0) next = cs[k];
-            else if (sp < kGridStack) { stk[sp] = cs[k]; sd[sp] = ds[k]; ++sp; }
-            else atomicOr(status, ST_STACK);
-        }
-        if (next >= 0) { node = next; continue; }
-        node = -1;
-        while (sp > 0) {
-            --sp;
-            if (sd[sp] <= kd[kKnn - 1]) { node = stk[sp]; break; }
-        }
-        if (node < 0) break;
-    }
+// Is the whole box (relative to the site: [bl, bh]) strictly nearer to the neighbour at
+// offset d = t - s?  A point x' (relative) is nearer to t iff 2 x'.d - |d|^2 > 0; the
+// minimum over the box picks each axis's end by the sign of d.  p.w = |d|^2 + margin.
+__device__ __forceinline__ bool box_beyond(float3 bl, float3 bh, float4 p) {
+    const float mx = p.x > 0.0f ? bl.x * p.x : bh.x * p.x;
+    const float my = p.y > 0.0f ? bl.y * p.y : bh.y * p.y;
+    const float mz = p.z > 0.0f ? bl.z * p.z : bh.z * p.z;
+    return 2.0f * (mx + my + mz) - p.w > 0.0f;
 }
 
-// Is the whole box strictly closer to site t than to site s?  max over the box of
-// 2 x.(s - t) + |t|^2 - |s|^2 must be < -margin.
-__device__ __forceinline__ bool box_closer_to(float3 lo, float3 hi, float3 s, float3 t, float margin) {
-    const float ax = 2.0f * (s.x - t.x), ay = 2.0f * (s.y - t.y), az = 2.0f * (s.z - t.z);
-    const float m = (ax > 0 ? ax * hi.x : ax * lo.x) + (ay > 0 ? ay * hi.y : ay * lo.y) + (az > 0 ? az * hi.z : az * lo.z);
-    const float v = m + (dot3(t, t) - dot3(s, s));
-    return v < -margin;
-}
-
-// Counting pass (FILL = false): count[cid] = the cell's candidates, the first kGridSlab of
-// them kept in slab[cid * kGridSlab ..].  Filling pass (FILL = true): the candidates of the
-// cells in `list` (those that overflowed the slab) written to out[off[cid] ..].
+// Rasterise the Voronoi cells of sites [0, n_sites) into the grid.  FILL = false: count the
+// candidates of every grid cell (cell_count) and of every site (site_count).  FILL = true:
+// write each site into its grid cells' lists (out_site at cell_off[c] + an atomic slot).
 template <bool FILL>
-__global__ void k_grid(GridParams g, const BNode* __restrict__ nodes, int root, const float4* __restrict__ sites,
-                       int n_sites, int64_t* __restrict__ count, float4* __restrict__ slab,
-                       const int64_t* __restrict__ list, int64_t n_list, const int64_t* __restrict__ off,
-                       float4* __restrict__ out, unsigned* status) {
-    const int64_t n_cells = (int64_t)g.G * g.G * g.G;
-    const int64_t n_work = FILL ? n_list : n_cells;
-    for (int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; w < n_work; w += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t cid = FILL ? list[w] : w;
-        const int ix = (int)(cid % g.G), iy = (int)((cid / g.G) % g.G), iz = (int)(cid / ((int64_t)g.G * g.G));
-        const float3 c = cell_centre(g, ix, iy, iz);
-        // the box is grown by 1% of a cell on every side: a query binned by FP32 rounding into
-        // a neighbouring cell still lies inside the box its candidates were chosen for
-        const float3 lo = make_float3(g.lo.x + (ix - 0.01f) * g.cell.x, g.lo.y + (iy - 0.01f) * g.cell.y,
-                                      g.lo.z + (iz - 0.01f) * g.cell.z);
-        const float3 hi = make_float3(g.lo.x + (ix + 1.01f) * g.cell.x, g.lo.y + (iy + 1.01f) * g.cell.y,
-                                      g.lo.z + (iz + 1.01f) * g.cell.z);
-        const float h = 0.5f * 1.02f * sqrtf(dot3(g.cell, g.cell));
-        float kd[kKnn];
-        int ki[kKnn];
-        knn(c, nodes, root, sites, kd, ki, status);
-        // range radius: d_nn + 2h, inflated so FP32 rounding never loses a site
-        const float R = (sqrtf(kd[0]) + 2.0f * h) * (1.0f + 1e-5f) + 1e-6f * h;
-        const float R2 = R * R;
-        int64_t k = 0;
-        const int64_t base = FILL ? off[cid] : 0;
-        auto consider = [&](int s) {
-            const float4 p = __ldg(sites + s);
-            const float3 ps = f3(p);
-            const float dx = ps.x - c.x, dy = ps.y - c.y, dz = ps.z - c.z;
-            if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) > R2) return;
-            for (int j = 0; j < kKnn; ++j) {
-                const int t = ki[j];
-                if (t < 0 || t == s) continue;
-                if (box_closer_to(lo, hi, ps, f3(__ldg(sites + t)), g.margin)) return;
-            }
-            // candidate stored with its coordinates (id in w) so a query reads one contiguous run
-            const float4 e = make_float4(ps.x, ps.y, ps.z, __int_as_float(s));
-            if (FILL) out[base + k] = e;
-            else if (k < kGridSlab) slab[cid * kGridSlab + k] = e;
-            ++k;
+__global__ void __launch_bounds__(32 * kRasterWarps)
+    k_grid_raster(RasterParams g, const float4* __restrict__ sites, int n_sites, const int64_t* __restrict__ nb_off,
+                  const int32_t* __restrict__ nb_id, const int4* __restrict__ root_box, int* __restrict__ cell_count,
+                  const int* __restrict__ cell_off, int* __restrict__ out_site, int* __restrict__ site_count,
+                  unsigned* status) {
+    __shared__ float4 planes[kRasterWarps][kRasterPlanes];
+    __shared__ unsigned long long stack[kRasterWarps][kRasterStack];
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const unsigned FULL = 0xffffffffu;
+    for (int s = blockIdx.x * kRasterWarps + w; s < n_sites; s += gridDim.x * kRasterWarps) {
+        const float4 sp = __ldg(sites + s);
+        const int64_t n0 = nb_off[s];
+        const int nn = (int)(nb_off[s + 1] - n0);
+        // bisector of (s, t) relative to s: d = t - s (exact for lattice sites), |d|^2 and a
+        // margin that covers the FP32 rounding of the test (|x'| <= the domain's extent)
+        auto plane_of = [&](int k) {
+            const float4 t = __ldg(sites + __ldg(nb_id + n0 + k));
+            const float dx = t.x - sp.x, dy = t.y - sp.y, dz = t.z - sp.z;
+            const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+            return make_float4(dx, dy, dz, dd + g.rel * fmaf(g.ext, sqrtf(dd), dd));
         };
-        if (root < 0) {
-            consider(~root);
-        } else {
-            int stk[kGridStack];
-            int sp = 0, node = root;
-            while (node >= 0) {
-                const float4* np = reinterpret_cast<const float4*>(nodes + node);
-                const float4 lo0 = __ldg(np), hi0 = __ldg(np + 1), lo1 = __ldg(np + 2), hi1 = __ldg(np + 3);
-                const int cs[2] = {__float_as_int(lo0.w), __float_as_int(lo1.w)};
-                const float ds[2] = {box_dist2(c, f3(lo0), f3(hi0)), box_dist2(c, f3(lo1), f3(hi1))};
-                int next = -1;
-                for (int hh = 0; hh < 2; ++hh) {
-                    if (ds[hh] > R2) continue;
-                    if (cs[hh] < 0) consider(~cs[hh]);
-                    else if (next < 0) next = cs[hh];
-                    else if (sp < kGridStack) stk[sp++] = cs[hh];
-                    else atomicOr(status, ST_STACK);
-                }
-                if (next < 0 && sp > 0) next = stk[--sp];
-                node = next;
+        // the nearest kRasterPlanes neighbours only (the lists are stored nearest first): a
+        // site with more neighbours (the centre of a co-spherical set has thousands) keeps a
+        // few extra grid cells but its rasterisation stays cheap
+        const int np = min(nn, kRasterPlanes);
+        __syncwarp();
+        for (int k = lane; k < np; k += 32) planes[w][k] = plane_of(k);
+        __syncwarp();
+        auto rejected = [&](int x0, int x1, int y0, int y1, int z0, int z1) {
+            const float3 bl = make_float3(fmaf((float)x0 - 0.01f, g.h.x, g.lo.x) - sp.x,
+                                          fmaf((float)y0 - 0.01f, g.h.y, g.lo.y) - sp.y,
+                                          fmaf((float)z0 - 0.01f, g.h.z, g.lo.z) - sp.z);
+            const float3 bh = make_float3(fmaf((float)x1 + 1.01f, g.h.x, g.lo.x) - sp.x,
+                                          fmaf((float)y1 + 1.01f, g.h.y, g.lo.y) - sp.y,
+                                          fmaf((float)z1 + 1.01f, g.h.z, g.lo.z) - sp.z);
+            for (int k = 0; k < np; ++k)
+                if (box_beyond(bl, bh, planes[w][k])) return true;
+            return false;
+        };
+        int emitted = 0;
+        auto emit = [&](int x, int y, int z) {
+            const int64_t c = ((int64_t)z * g.G + y) * g.G + x;
+            if (FILL) out_site[cell_off[c] + atomicAdd(cell_count + c, 1)] = s;
+            else atomicAdd(cell_count + c, 1);
+            ++emitted;
+        };
+        const int4 rb = __ldg(root_box + s);  // (x0 | x1 << 16, y0 | y1 << 16, z0 | z1 << 16, valid)
+        int sp_top = 0;
+        if (rb.w) {
+            if (lane == 0)
+                stack[w][0] = pack_box(rb.x & 0xffff, rb.x >> 16, rb.y & 0xffff, rb.y >> 16, rb.z & 0xffff, rb.z >> 16);
+            sp_top = 1;
+        }
+        __syncwarp();
+        while (sp_top > 0) {
+            const int take = min(sp_top, 32);
+            sp_top -= take;
+            unsigned long long b = 0;
+            if (lane < take) b = stack[w][sp_top + lane];
+            __syncwarp();
+            int x0 = (int)(b & 1023), x1 = (int)((b >> 10) & 1023), y0 = (int)((b >> 20) & 1023),
+                y1 = (int)((b >> 30) & 1023), z0 = (int)((b >> 40) & 1023), z1 = (int)((b >> 50) & 1023);
+            bool split = false;
+            if (lane < take && !rejected(x0, x1, y0, y1, z0, z1)) {
+                if (x0 == x1 && y0 == y1 && z0 == z1) emit(x0, y0, z0);
+                else split = true;
             }
+            // children of the surviving boxes go on the stack (two each), as room allows
+            const unsigned m = __ballot_sync(FULL, split);
+            const int rank = __popc(m & ((1u << lane) - 1u));
+            const bool room = sp_top + 2 * (rank + 1) <= kRasterStack;
+            if (split && room) {
+                const int ex = x1 - x0, ey = y1 - y0, ez = z1 - z0;
+                unsigned long long c0, c1;
+                if (ex >= ey && ex >= ez) {
+                    const int mid = x0 + ex / 2;
+                    c0 = pack_box(x0, mid, y0, y1, z0, z1);
+                    c1 = pack_box(mid + 1, x1, y0, y1, z0, z1);
+                } else if (ey >= ez) {
+                    const int mid = y0 + ey / 2;
+                    c0 = pack_box(x0, x1, y0, mid, z0, z1);
+                    c1 = pack_box(x0, x1, mid + 1, y1, z0, z1);
+                } else {
+                    const int mid = z0 + ez / 2;
+                    c0 = pack_box(x0, x1, y0, y1, z0, mid);
+                    c1 = pack_box(x0, x1, y0, y1, mid + 1, z1);
+                }
+                stack[w][sp_top + 2 * rank] = c0;
+                stack[w][sp_top + 2 * rank + 1] = c1;
+            } else if (split) {
+                // no room: test this box's grid cells one by one (slower, same result)
+                for (int z = z0; z <= z1; ++z)
+                    for (int y = y0; y <= y1; ++y)
+                        for (int x = x0; x <= x1; ++x)
+                            if (!rejected(x, x, y, y, z, z)) emit(x, y, z);
+            }
+            sp_top += 2 * __popc(__ballot_sync(FULL, split && room));
+            __syncwarp();
         }
-        if (!FILL) count[cid] = k;
-        else if (k != off[cid + 1] - off[cid]) atomicOr(status, ST_BAD);
+        for (int o = 16; o > 0; o >>= 1) emitted += __shfl_xor_sync(FULL, emitted, o);
+        if (lane == 0) {
+            if (!FILL) site_count[s] = emitted;
+            else if (emitted != site_count[s]) atomicOr(status, ST_BAD);  // both passes walk alike
+        }
     }
 }
 
-__global__ void k_i64_to_i32(const int64_t* __restrict__ a, int32_t* __restrict__ b, int64_t n);
-
-// Copies the slab-held candidates of every cell that fit into the slab to their CSR slots;
-// the cells that overflowed are appended to `list` for the filling pass.
-__global__ void k_grid_pack(const float4* __restrict__ slab, const int64_t* __restrict__ count,
-                            const int64_t* __restrict__ off, int64_t n_cells, float4* __restrict__ out,
-                            int64_t* __restrict__ list, unsigned long long* __restrict__ n_list) {
-    for (int64_t c = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; c < n_cells; c += (int64_t)gridDim.x * blockDim.x) {
-        const int64_t k = count[c];
-        if (k > kGridSlab) {
-            list[atomicAdd(n_list, 1ull)] = c;
-            continue;
-        }
-        for (int64_t j = 0; j < k; ++j) out[off[c] + j] = slab[c * kGridSlab + j];
+// Candidate entries (site xyz, site id in w) from the sorted site ids.
+__global__ void k_grid_pack(const int* __restrict__ ids, int64_t n, const float4* __restrict__ sites,
+                            float4* __restrict__ out) {
+    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
+        const int s = ids[j];
+        const float4 p = __ldg(sites + s);
+        out[j] = make_float4(p.x, p.y, p.z, __int_as_float(s));
     }
 }
 
-int build_grid(MeshData& m, const Bvh& site_bvh, int G, unsigned* status, cudaStream_t s) {
+int build_grid(MeshData& m, const SiteSet& ss, int G, unsigned* status, cudaStream_t s) {
+    if (G < 1 || G > 1023) return fail(P2M_ERR_INVALID_ARG, "nearest-site grid resolution must be 1..1023");
     const int64_t n_cells = (int64_t)G * G * G;
-    GridParams g;
+    const int S = (int)(m.site_pos.size() / 3);
+    RasterParams g;
     g.G = G;
     g.lo = make_float3((float)m.dom_lo[0], (float)m.dom_lo[1], (float)m.dom_lo[2]);
-    g.cell = make_float3((float)((m.dom_hi[0] - m.dom_lo[0]) / G), (float)((m.dom_hi[1] - m.dom_lo[1]) / G),
-                         (float)((m.dom_hi[2] - m.dom_lo[2]) / G));
-    double scale = 0;
-    for (int k = 0; k < 3; ++k) scale = std::max(scale, std::max(std::fabs(m.dom_lo[k]), std::fabs(m.dom_hi[k])));
-    g.margin = (float)(64.0 * 1.2e-7 * 4.0 * scale * scale);
-    DevBuf cnt, off;
-    P2M_TRY(cnt.alloc(sizeof(int64_t) * (n_cells + 1)));
-    P2M_TRY(off.alloc(sizeof(int64_t) * (n_cells + 1)));
-    const int n_sites = (int)(m.site_pos.size() / 3);
-    const BNode* nodes = site_bvh.nodes.as<const BNode>();
-    const int blocks = (int)std::min<int64_t>((n_cells + 127) / 128, 152 * 32);
-    DevBuf slab;
-    P2M_TRY(slab.alloc(sizeof(float4) * kGridSlab * n_cells));
-    k_grid<false><<<blocks, 128, 0, s>>>(g, nodes, site_bvh.root, m.d_sites.as<float4>(), n_sites, cnt.as<int64_t>(),
-                                         slab.as<float4>(), nullptr, 0, nullptr, nullptr, status);
+    g.h = make_float3((float)((m.dom_hi[0] - m.dom_lo[0]) / G), (float)((m.dom_hi[1] - m.dom_lo[1]) / G),
+                      (float)((m.dom_hi[2] - m.dom_lo[2]) / G));
+    // The test value 2 x'.d - |d|^2 is at most a few (|x'| |d| + |d|^2) in size, with |x'| up
+    // to the extent E of D; each FP32 operation adds a relative 2^-24, the box corners x'
+    // carry an absolute error of a few ulp(E).  A margin of 2^-14 (E |d| + |d|^2) is a wide
+    // cover (it moves the bisector by at most ~2^-15 E, far below a grid cell).
+    double ext = 0;
+    for (int k = 0; k < 3; ++k) ext = std::max(ext, std::max(std::fabs(m.dom_lo[k]), std::fabs(m.dom_hi[k])));
+    ext = std::max(ext, m.diag);
+    g.ext = (float)ext;
+    g.rel = (float)std::ldexp(1.0, -14);
+    // the per-site root boxes (grid indices around the cell's corners, one cell of margin
+    // against rounding) and the neighbour CSR
+    std::vector<int4> rb(S);
+    {
+        std::atomic<int> next(0);
+        auto work = [&]() {
+            while (true) {
+                const int i0 = next.fetch_add(1024);
+                if (i0 >= S) break;
+                for (int i = i0; i < std::min(S, i0 + 1024); ++i) {
+                    const int64_t c0 = ss.cell_off[i], c1 = ss.cell_off[i + 1];
+                    if (c1 <= c0) { rb[i] = make_int4(0, 0, 0, 0); continue; }
+                    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+                    for (int64_t c = c0; c < c1; ++c)
+                        for (int k = 0; k < 3; ++k) {
+                            lo[k] = std::min(lo[k], ss.cell_xyz[3 * c + k]);
+                            hi[k] = std::max(hi[k], ss.cell_xyz[3 * c + k]);
+                        }
+                    int a[3], b[3];
+                    for (int k = 0; k < 3; ++k) {
+                        const double hk = (m.dom_hi[k] - m.dom_lo[k]) / G;
+                        a[k] = (int)std::floor((lo[k] - m.dom_lo[k]) / hk) - 1;
+                        b[k] = (int)std::floor((hi[k] - m.dom_lo[k]) / hk) + 1;
+                        a[k] = std::max(0, std::min(G - 1, a[k]));
+                        b[k] = std::max(0, std::min(G - 1, b[k]));
+                    }
+                    rb[i] = make_int4(a[0] | (b[0] << 16), a[1] | (b[1] << 16), a[2] | (b[2] << 16), 1);
+                }
+            }
+        };
+        std::vector<std::thread> th;
+        for (int t = 0; t < std::max(1, std::min(hardware_threads(), (S + 1023) / 1024)); ++t) th.emplace_back(work);
+        for (auto& t : th) t.join();
+    }
+    const int64_t nnb = ss.nb_off[S];
+    DevBuf d_rb, d_nboff, d_nb, d_count, d_off, d_site_count, d_ids, d_ids2, tmp;
+    P2M_TRY(d_rb.alloc(sizeof(int4) * S));
+    P2M_TRY(d_nboff.alloc(sizeof(int64_t) * (S + 1)));
+    P2M_TRY(d_nb.alloc(sizeof(int32_t) * std::max<int64_t>(nnb, 1)));
+    P2M_TRY(d_count.alloc(sizeof(int) * (n_cells + 1)));
+    P2M_TRY(d_off.alloc(sizeof(int) * (n_cells + 1)));
+    P2M_TRY(d_site_count.alloc(sizeof(int) * S));
+    P2M_CUDA_TRY(cudaMemcpyAsync(d_rb.p, rb.data(), sizeof(int4) * S, cudaMemcpyHostToDevice, s));
+    P2M_CUDA_TRY(cudaMemcpyAsync(d_nboff.p, ss.nb_off.data(), sizeof(int64_t) * (S + 1), cudaMemcpyHostToDevice, s));
+    if (nnb > 0) P2M_CUDA_TRY(cudaMemcpyAsync(d_nb.p, ss.nb_id.data(), sizeof(int32_t) * nnb, cudaMemcpyHostToDevice, s));
+    P2M_CUDA_TRY(cudaMemsetAsync(d_count.p, 0, sizeof(int) * (n_cells + 1), s));
+    const int blocks = std::max(1, std::min((S + kRasterWarps - 1) / kRasterWarps, sm_count() * 16));
+    const float4* sites = m.d_sites.as<float4>();
+    k_grid_raster<false><<<blocks, 32 * kRasterWarps, 0, s>>>(g, sites, S, d_nboff.as<int64_t>(), d_nb.as<int32_t>(),
+                                                               d_rb.as<int4>(), d_count.as<int>(), nullptr, nullptr,
+                                                               d_site_count.as<int>(), status);
     P2M_CUDA_TRY(cudaGetLastError());
-    P2M_CUDA_TRY(cudaMemsetAsync(cnt.as<int64_t>() + n_cells, 0, sizeof(int64_t), s));
-    DevBuf tmp;
-    size_t tb = 0;
-    P2M_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, tb, cnt.as<int64_t>(), off.as<int64_t>(), n_cells + 1, s));
-    P2M_TRY(tmp.alloc(tb + 16));
-    P2M_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp.p, tb, cnt.as<int64_t>(), off.as<int64_t>(), n_cells + 1, s));
-    int64_t total = 0;
-    P2M_CUDA_TRY(cudaMemcpyAsync(&total, off.as<int64_t>() + n_cells, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
+    size_t tb = 0, tb2 = 0;
+    P2M_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, tb, d_count.as<int>(), d_off.as<int>(), (int)(n_cells + 1), s));
+    // the count could exceed int32 only for absurd grids; it is checked below on the int64 sum
+    std::vector<int> cnt(n_cells);
+    P2M_CUDA_TRY(cudaMemcpyAsync(cnt.data(), d_count.p, sizeof(int) * n_cells, cudaMemcpyDeviceToHost, s));
     P2M_CUDA_TRY(cudaStreamSynchronize(s));
+    int64_t total = 0, mx = 0;
+    for (int64_t c = 0; c < n_cells; ++c) {
+        total += cnt[c];
+        mx = std::max<int64_t>(mx, cnt[c]);
+    }
     if (total > 0x7fffffffLL) return fail(P2M_ERR_LIMIT, "nearest-site grid too large");
-    P2M_TRY(m.d_cell_site.alloc(sizeof(float4) * std::max<int64_t>(total, 1)));
-    P2M_TRY(m.d_cell_off.alloc(sizeof(int32_t) * (n_cells + 1)));
-    // cells within the slab are copied; the rest (cells with more than kGridSlab candidates)
-    // run the search again, writing straight to their slots
-    DevBuf list, n_list;
-    P2M_TRY(list.alloc(sizeof(int64_t) * std::max<int64_t>(n_cells, 1)));
-    P2M_TRY(n_list.alloc(sizeof(unsigned long long)));
-    P2M_CUDA_TRY(cudaMemsetAsync(n_list.p, 0, sizeof(unsigned long long), s));
-    k_grid_pack<<<blocks, 128, 0, s>>>(slab.as<float4>(), cnt.as<int64_t>(), off.as<int64_t>(), n_cells,
-                                       m.d_cell_site.as<float4>(), list.as<int64_t>(), n_list.as<unsigned long long>());
+    P2M_CUDA_TRY(cub::DeviceSegmentedSort::SortKeys(nullptr, tb2, (const int*)nullptr, (int*)nullptr, (int)total,
+                                                    (int)n_cells, (const int*)nullptr, (const int*)nullptr, s));
+    P2M_TRY(tmp.alloc(std::max(tb, tb2) + 16));
+    P2M_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp.p, tb, d_count.as<int>(), d_off.as<int>(), (int)(n_cells + 1), s));
+    P2M_TRY(d_ids.alloc(sizeof(int) * std::max<int64_t>(total, 1)));
+    P2M_TRY(d_ids2.alloc(sizeof(int) * std::max<int64_t>(total, 1)));
+    P2M_CUDA_TRY(cudaMemsetAsync(d_count.p, 0, sizeof(int) * (n_cells + 1), s));
+    k_grid_raster<true><<<blocks, 32 * kRasterWarps, 0, s>>>(g, sites, S, d_nboff.as<int64_t>(), d_nb.as<int32_t>(),
+                                                              d_rb.as<int4>(), d_count.as<int>(), d_off.as<int>(),
+                                                              d_ids.as<int>(), d_site_count.as<int>(), status);
     P2M_CUDA_TRY(cudaGetLastError());
-    unsigned long long n_over = 0;
-    P2M_CUDA_TRY(cudaMemcpyAsync(&n_over, n_list.p, sizeof(n_over), cudaMemcpyDeviceToHost, s));
-    P2M_CUDA_TRY(cudaStreamSynchronize(s));
-    slab.release();
-    if (n_over > 0) {
-        const int ob = (int)std::min<int64_t>(((int64_t)n_over + 127) / 128, 152 * 32);
-        k_grid<true><<<ob, 128, 0, s>>>(g, nodes, site_bvh.root, m.d_sites.as<float4>(), n_sites, nullptr, nullptr,
-                                        list.as<int64_t>(), (int64_t)n_over, off.as<int64_t>(),
-                                        m.d_cell_site.as<float4>(), status);
+    if (total > 0)
+        P2M_CUDA_TRY(cub::DeviceSegmentedSort::SortKeys(tmp.p, tb2, d_ids.as<int>(), d_ids2.as<int>(), (int)total,
+                                                        (int)n_cells, d_off.as<int>(), d_off.as<int>() + 1, s));
+    P2M_TRY(m.d_cell_site.alloc(sizeof(float4) * std::max<int64_t>(total, 1)));
+    if (total > 0) {
+        k_grid_pack<<<(int)std::min<int64_t>((total + 255) / 256, (int64_t)sm_count() * 32), 256, 0, s>>>(
+            d_ids2.as<int>(), total, sites, m.d_cell_site.as<float4>());
         P2M_CUDA_TRY(cudaGetLastError());
     }
-    k_i64_to_i32<<<256, 256, 0, s>>>(off.as<int64_t>(), m.d_cell_off.as<int32_t>(), n_cells + 1);
-    P2M_CUDA_TRY(cudaGetLastError());
-    std::vector<int64_t> c(n_cells);
-    P2M_CUDA_TRY(cudaMemcpyAsync(c.data(), cnt.p, sizeof(int64_t) * n_cells, cudaMemcpyDeviceToHost, s));
+    m.d_cell_off = std::move(d_off);
     P2M_CUDA_TRY(cudaStreamSynchronize(s));
-    int64_t mx = 0;
-    for (int64_t x : c) mx = std::max(mx, x);
     m.G = G;
     m.g_lo = g.lo;
     m.g_hi = make_float3((float)m.dom_hi[0], (float)m.dom_hi[1], (float)m.dom_hi[2]);
-    m.g_inv_h = make_float3(1.0f / g.cell.x, 1.0f / g.cell.y, 1.0f / g.cell.z);
+    m.g_inv_h = make_float3(1.0f / g.h.x, 1.0f / g.h.y, 1.0f / g.h.z);
     m.stats.grid_res = G;
     m.stats.grid_entries = total;
     m.stats.grid_max = mx;

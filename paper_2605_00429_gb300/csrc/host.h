@@ -64,6 +64,10 @@ namespace p2m {
 unsigned* index_status(p2m_index* h);
 DevBuf& index_rest(p2m_index* h);  // scratch for the compacted out-of-domain query list
 int check_status_word(p2m_index* h, cudaStream_t s, const char* what);
+// Checks shared by the entry points that launch work on an index: the device the index was
+// built on must be current (its buffers live there), and a call takes at most 2^31 - 1
+// points (query positions are int32 inside the kernels).
+int check_call(const p2m_index* h, int64_t n, const char* what);
 
 // Sites, Delaunay, augmentation, corner balls, interception lists, nearest-site grid.
 int build_partition(MeshData& m, const p2m_build_params& prm, p2m_index* h, cudaStream_t s);

@@ -287,7 +287,7 @@ int build_lists(MeshData& m, const float4* d_balls, const int64_t* d_ball_off, i
     DevBuf cnt, off64, tmp;
     P2M_TRY(cnt.alloc(sizeof(int64_t) * (n_sites + 1)));
     P2M_TRY(off64.alloc(sizeof(int64_t) * (n_sites + 1)));
-    const int blocks = std::max(1, std::min((n_sites + kListWarps - 1) / kListWarps, 152 * 16));
+    const int blocks = std::max(1, std::min((n_sites + kListWarps - 1) / kListWarps, sm_count() * 16));
     const MeshView v = m.view();
     k_lists<false><<<blocks, 32 * kListWarps, 0, s>>>(d_balls, d_ball_off, n_sites, v.bvh, v.bvh_root, v.tri,
                                                      cnt.as<int64_t>(), nullptr, nullptr, status);
@@ -313,7 +313,7 @@ int build_lists(MeshData& m, const float4* d_balls, const int64_t* d_ball_off, i
     P2M_CUDA_TRY(cudaGetLastError());
     // entry keys; lists scanned per thread are sorted by key (nearest first)
     {
-        const int kb = std::max(1, std::min((n_sites + 7) / 8, 152 * 16));
+        const int kb = std::max(1, std::min((n_sites + 7) / 8, sm_count() * 16));
         P2M_TRY(m.d_row_key.alloc(sizeof(float) * std::max<int64_t>(nnz, 1)));
         k_entry_keys<<<kb, 256, 0, s>>>(off64.as<int64_t>(), n_sites, m.d_row_tri.as<int32_t>(), m.d_refs.as<float4>(),
                                         m.d_tsph.as<float4>(), m.d_row_key.as<float>());
@@ -365,7 +365,7 @@ int build_lists(MeshData& m, const float4* d_balls, const int64_t* d_ball_off, i
         double scale = m.diag;
         for (int k = 0; k < 3; ++k) scale = std::max(scale, std::max(std::fabs(m.bb_lo[k]), std::fabs(m.bb_hi[k])));
         const float pad = (float)(scale * std::ldexp(1.0, -20));
-        k_chunk_boxes<<<std::max(1, std::min((n_sites + 7) / 8, 152 * 16)), 256, 0, s>>>(
+        k_chunk_boxes<<<std::max(1, std::min((n_sites + 7) / 8, sm_count() * 16)), 256, 0, s>>>(
             off64.as<int64_t>(), m.d_chunk_off.as<int32_t>(), n_sites, m.d_row_tri.as<int32_t>(), m.d_tlo.as<float4>(),
             m.d_thi.as<float4>(), m.d_tri.as<float4>(), pad, m.d_cbox.as<float4>());
         P2M_CUDA_TRY(cudaGetLastError());
@@ -380,14 +380,14 @@ int build_lists(MeshData& m, const float4* d_balls, const int64_t* d_ball_off, i
         P2M_CUDA_TRY(cudaMemcpyAsync(&n1, m.d_l1_off.as<int32_t>() + n_sites, sizeof(int32_t), cudaMemcpyDeviceToHost, s));
         P2M_CUDA_TRY(cudaStreamSynchronize(s));
         P2M_TRY(m.d_l1box.alloc(sizeof(float4) * 2 * std::max<int32_t>(n1, 1)));
-        k_parent_boxes<<<std::max(1, std::min((n_sites + 7) / 8, 152 * 16)), 256, 0, s>>>(
+        k_parent_boxes<<<std::max(1, std::min((n_sites + 7) / 8, sm_count() * 16)), 256, 0, s>>>(
             m.d_chunk_off.as<int32_t>(), m.d_l1_off.as<int32_t>(), n_sites, m.d_cbox.as<float4>(), m.d_l1box.as<float4>());
         P2M_CUDA_TRY(cudaGetLastError());
     }
     // the entries as (triangle, key) pairs; the separate arrays are released
     P2M_TRY(m.d_row_ent.alloc(sizeof(int2) * std::max<int64_t>(nnz, 1)));
     if (nnz > 0) {
-        k_pack_entries<<<(int)std::min<int64_t>((nnz + 255) / 256, 152 * 32), 256, 0, s>>>(
+        k_pack_entries<<<(int)std::min<int64_t>((nnz + 255) / 256, sm_count() * 32), 256, 0, s>>>(
             m.d_row_tri.as<int32_t>(), m.d_row_key.as<float>(), nnz, m.d_row_ent.as<int2>());
         P2M_CUDA_TRY(cudaGetLastError());
     }

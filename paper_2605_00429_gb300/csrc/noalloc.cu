@@ -58,6 +58,8 @@ extern "C" int p2m_query_noalloc(p2m_index* h, const float* d_pts, int64_t n, fl
                                        " queries per call (got " + std::to_string(n) + "); split the batch");
     if (n == 0) return P2M_OK;
     if (!d_pts || !d_dist) return fail(P2M_ERR_INVALID_ARG, "d_pts and d_dist must be non-NULL");
+    // the index's device must be current: the scratch address below is the current device's
+    P2M_TRY(check_call(h, n, "p2m_query_noalloc"));
     void* base = nullptr;
     P2M_TRY(scratch_address(&base));
     char* b = static_cast<char*>(base);

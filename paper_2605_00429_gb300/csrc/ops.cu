@@ -11,13 +11,55 @@ namespace p2m {
 
 // K4: gradient of sum_i g_i d(q_i, M) through the closest point p = sum_k b_k v_k of the
 // forward pass:  dd/dq = (q - p)/d,  dd/dv_k = -b_k (q - p)/d  (0 where d = 0).
-// Vertex sums either use float atomics, or 2^-32 fixed point in 64-bit integer atomics,
-// whose sum does not depend on the order of the additions (bit-reproducible).
+// Vertex sums either use float atomics, or fixed point in 64-bit integer atomics, whose sum
+// does not depend on the order of the additions (bit-reproducible).  The fixed-point unit is
+// 2^-e with e chosen per call from bound = max_i |g_i| max_k |b_k|: a contribution is at most
+// bound in magnitude (|q - p| / d = 1), a vertex coordinate receives at most 3n of them (three
+// per query when a triangle repeats a vertex), and e makes 3n * bound * 2^e <= 2^62, so no
+// vertex sum can overflow.  Each contribution is rounded to the unit, an absolute error of at
+// most 2^-(e+1) <= 3n * bound * 2^-63.
+__global__ void k_grad_bound(const float* __restrict__ gdist, const float* __restrict__ bary, int64_t n,
+                             unsigned* __restrict__ bound_bits) {
+    float m = 0.0f;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float b = fmaxf(fabsf(bary[3 * i]), fmaxf(fabsf(bary[3 * i + 1]), fabsf(bary[3 * i + 2])));
+        const float c = fabsf(gdist[i]) * fmaxf(b, 1.0f);
+        // NaN is kept (its bits order above infinity) so the caller sees a non-finite bound
+        m = (c > m || c != c) ? c : m;
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+        const float x = __shfl_xor_sync(0xffffffffu, m, o);
+        m = (x > m || x != x) ? x : m;
+    }
+    if ((threadIdx.x & 31) == 0) atomicMax(bound_bits, __float_as_uint(m));  // |x| >= 0: bits order as uint
+}
+
+// Exponent e of the fixed-point unit 2^-e for n contributions of magnitude <= bound; 0 when
+// every contribution is 0; -1000 when the bound is not finite (the caller flags it).
+__device__ __forceinline__ int grad_exponent(unsigned bound_bits, int64_t n) {
+    const float bound = __uint_as_float(bound_bits);
+    if (!(bound <= 3.0e38f)) return -1000;
+    if (bound == 0.0f) return 0;
+    int ex;
+    frexp((double)bound * (double)n * 1.0001, &ex);  // bound * n * 1.0001 < 2^ex
+    return 62 - ex;
+}
+
 template <bool DET>
 __global__ void k_backward(const float* __restrict__ verts, const int32_t* __restrict__ tris,
                            const float* __restrict__ pts, int64_t n, const int32_t* __restrict__ tri,
                            const float* __restrict__ bary, const float* __restrict__ gdist, float* __restrict__ gpts,
-                           float* __restrict__ gverts, unsigned long long* __restrict__ gacc, int n_tris) {
+                           float* __restrict__ gverts, unsigned long long* __restrict__ gacc,
+                           const unsigned* __restrict__ bound_bits, int n_tris, unsigned* status) {
+    double scale = 0.0;
+    if (DET) {
+        const int e = grad_exponent(*bound_bits, 3 * n);  // a vertex gets at most 3 per query
+        if (e == -1000) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(status, ST_LIMIT);
+            return;
+        }
+        scale = ldexp(1.0, e);
+    }
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int f = tri[i];
         const float3 q = make_float3(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]);
@@ -45,7 +87,7 @@ __global__ void k_backward(const float* __restrict__ verts, const int32_t* __res
                 const float c[3] = {-b[k] * u.x, -b[k] * u.y, -b[k] * u.z};
                 for (int a = 0; a < 3; ++a) {
                     if (DET) {
-                        const long long fx = __double2ll_rn((double)c[a] * 4294967296.0);
+                        const long long fx = __double2ll_rn((double)c[a] * scale);
                         atomicAdd(gacc + 3 * (int64_t)vi[k] + a, (unsigned long long)fx);
                     } else {
                         atomicAdd(gverts + 3 * (int64_t)vi[k] + a, c[a]);
@@ -56,9 +98,13 @@ __global__ void k_backward(const float* __restrict__ verts, const int32_t* __res
     }
 }
 
-__global__ void k_fixed_to_float_add(const unsigned long long* __restrict__ acc, float* __restrict__ out, int64_t n) {
+__global__ void k_fixed_to_float_add(const unsigned long long* __restrict__ acc, const unsigned* __restrict__ bound_bits,
+                                     int64_t n_contrib, float* __restrict__ out, int64_t n) {
+    const int e = grad_exponent(*bound_bits, n_contrib);
+    if (e == -1000) return;
+    const double unit = ldexp(1.0, -e);
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
-        out[i] += (float)((double)(long long)acc[i] * (1.0 / 4294967296.0));
+        out[i] += (float)((double)(long long)acc[i] * unit);
 }
 
 // Sign of the distance from the closest feature's pseudonormal.  The feature comes from the
@@ -170,13 +216,14 @@ int p2m_mesh_distance(p2m_index* h, const float* d_verts_b, int64_t n_verts_b, c
         return fail(P2M_ERR_INVALID_ARG, "bad mesh B or subdivisions (0..64)");
     cudaStream_t s = (cudaStream_t)stream;
     MeshData& m = *h->meshes[0];
+    P2M_TRY(check_call(h, n_tris_b * ((subdivisions + 1) * (subdivisions + 2) / 2 + 3), "p2m_mesh_distance"));
     const int per = subdivisions == 0 ? 3 : (subdivisions + 1) * (subdivisions + 2) / 2;
     const int64_t n = n_tris_b * per;
     DevBuf pts, dist, stats;
     P2M_TRY(pts.alloc(sizeof(float) * 3 * n));
     P2M_TRY(dist.alloc(sizeof(float) * n));
     P2M_TRY(stats.alloc(64));
-    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 32);
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, sm_count() * 32);
     k_mesh_samples<<<blocks, 256, 0, s>>>(d_verts_b, d_tris_b, n_tris_b, subdivisions, pts.as<float>());
     P2M_CUDA_TRY(cudaGetLastError());
     P2M_TRY(run_query(h, m, pts.as<float>(), n, dist.as<float>(), nullptr, nullptr, nullptr, nullptr, h->scratch_idx, s));
@@ -211,6 +258,7 @@ int p2m_query_signed(p2m_index* h, const float* d_pts, int64_t n, float* d_sdist
     if (n < 0) return fail(P2M_ERR_INVALID_ARG, "n < 0");
     if (n == 0) return P2M_OK;
     if (!d_pts || !d_sdist) return fail(P2M_ERR_INVALID_ARG, "d_pts and d_sdist must be non-NULL");
+    P2M_TRY(check_call(h, n, "p2m_query_signed"));
     cudaStream_t s = (cudaStream_t)stream;
     MeshData& m = *h->meshes[0];
     // the sign needs the triangle and barycentrics: use the caller's buffers or scratch
@@ -222,7 +270,7 @@ int p2m_query_signed(p2m_index* h, const float* d_pts, int64_t n, float* d_sdist
         if (!bary) bary = reinterpret_cast<float*>(h->sign_scratch.as<char>() + ((sizeof(int32_t) * n + 255) / 256) * 256);
     }
     P2M_TRY(run_query(h, m, d_pts, n, d_sdist, d_closest, tri, bary, nullptr, h->scratch_idx, s));
-    const int blocks = (int)std::min<int64_t>((n + 255) / 256, 152 * 32);
+    const int blocks = (int)std::min<int64_t>((n + 255) / 256, sm_count() * 32);
     k_sign<<<blocks, 256, 0, s>>>(m.d_verts.as<float>(), m.d_tris.as<int32_t>(), m.d_snorm.as<float4>(),
                                   m.d_vnorm.as<float4>(), d_pts, n, tri, bary, d_sdist, (int)m.n_tris);
     P2M_CUDA_TRY(cudaGetLastError());
@@ -235,28 +283,35 @@ int p2m_backward(p2m_index* h, const float* d_pts, int64_t n, const int32_t* d_t
     if (n < 0) return fail(P2M_ERR_INVALID_ARG, "n < 0");
     if (n == 0) return P2M_OK;
     if (!d_pts || !d_tri || !d_bary || !d_grad_dist) return fail(P2M_ERR_INVALID_ARG, "NULL input");
+    P2M_TRY(check_call(h, 0, "p2m_backward"));
     cudaStream_t s = (cudaStream_t)stream;
     MeshData& m = *h->meshes[0];
     const int64_t nv3 = m.n_verts * 3;
     const bool det = h->params.deterministic && d_grad_verts;
-    if (det) {
-        P2M_TRY(h->grad_acc.ensure(sizeof(unsigned long long) * nv3));
-        P2M_CUDA_TRY(cudaMemsetAsync(h->grad_acc.p, 0, sizeof(unsigned long long) * nv3, s));
-    }
     const int threads = 256;
-    const int blocks = (int)std::min<int64_t>((n + threads - 1) / threads, 152 * 32);
+    const int blocks = (int)std::min<int64_t>((n + threads - 1) / threads, sm_count() * 32);
+    unsigned* bound = nullptr;
+    if (det) {
+        // accumulator [nv3] int64, then the contribution bound word
+        P2M_TRY(h->grad_acc.ensure(sizeof(unsigned long long) * nv3 + 16));
+        P2M_CUDA_TRY(cudaMemsetAsync(h->grad_acc.p, 0, sizeof(unsigned long long) * nv3 + 16, s));
+        bound = reinterpret_cast<unsigned*>(h->grad_acc.as<unsigned long long>() + nv3);
+        k_grad_bound<<<blocks, threads, 0, s>>>(d_grad_dist, d_bary, n, bound);
+        P2M_CUDA_TRY(cudaGetLastError());
+    }
     if (det)
         k_backward<true><<<blocks, threads, 0, s>>>(m.d_verts.as<float>(), m.d_tris.as<int32_t>(), d_pts, n, d_tri, d_bary,
                                                      d_grad_dist, d_grad_pts, d_grad_verts,
-                                                     h->grad_acc.as<unsigned long long>(), (int)m.n_tris);
+                                                     h->grad_acc.as<unsigned long long>(), bound, (int)m.n_tris,
+                                                     index_status(h));
     else
         k_backward<false><<<blocks, threads, 0, s>>>(m.d_verts.as<float>(), m.d_tris.as<int32_t>(), d_pts, n, d_tri,
-                                                      d_bary, d_grad_dist, d_grad_pts, d_grad_verts, nullptr,
-                                                      (int)m.n_tris);
+                                                      d_bary, d_grad_dist, d_grad_pts, d_grad_verts, nullptr, nullptr,
+                                                      (int)m.n_tris, index_status(h));
     P2M_CUDA_TRY(cudaGetLastError());
     if (det) {
         k_fixed_to_float_add<<<(int)std::min<int64_t>((nv3 + 255) / 256, 4096), 256, 0, s>>>(
-            h->grad_acc.as<unsigned long long>(), d_grad_verts, nv3);
+            h->grad_acc.as<unsigned long long>(), bound, 3 * n, d_grad_verts, nv3);
         P2M_CUDA_TRY(cudaGetLastError());
     }
     return P2M_OK;
@@ -268,6 +323,7 @@ int p2m_query_host(p2m_index* h, const float* h_pts, int64_t n, float* h_dist, f
     if (n < 0) return fail(P2M_ERR_INVALID_ARG, "n < 0");
     if (n == 0) return P2M_OK;
     if (!h_pts || !h_dist) return fail(P2M_ERR_INVALID_ARG, "h_pts and h_dist must be non-NULL");
+    P2M_TRY(check_call(h, 0, "p2m_query_host"));
     MeshData& m = *h->meshes[0];
     cudaStream_t user = (cudaStream_t)stream;
     constexpr int kSlots = p2m_index::kPipe;

@@ -16,6 +16,9 @@ namespace p2m {
 void set_error(const std::string& msg);
 bool inject_fault(const char* what);  // P2M_FAULT == what (host-side test fault injection)
 int fail(int code, const std::string& msg);
+// Streaming multiprocessors of the current device (cached per device); launch grids are
+// sized in multiples of it.
+int sm_count();
 
 #define P2M_CUDA_TRY(expr)                                                              \
     do {                                                                                \
@@ -136,6 +139,7 @@ struct MeshData {
     int long_row = 256;
     bool sorted = true;          // process queries in grid-cell Morton order
     bool site_sorted = false;    // then regroup them by nearest site before the list scan
+    bool site_staged = false;    // queries counting-sorted by nearest site, lists staged in shared memory
     int G = 0;
     float3 g_lo{}, g_hi{}, g_inv_h{};
     p2m_stats stats{};

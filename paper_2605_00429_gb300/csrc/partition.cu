@@ -20,7 +20,7 @@ namespace p2m {
 
 int build_lists(MeshData& m, const float4* d_balls, const int64_t* d_ball_off, int n_sites, unsigned* status,
                 cudaStream_t s);
-int build_grid(MeshData& m, const Bvh& site_bvh, int G, unsigned* status, cudaStream_t s);
+int build_grid(MeshData& m, const SiteSet& ss, int G, unsigned* status, cudaStream_t s);
 
 static double ms_now() {
     using namespace std::chrono;
@@ -366,7 +366,8 @@ int build_partition(MeshData& m, const p2m_build_params& prm, p2m_index* h, cuda
         P2M_CUDA_TRY(cudaMemcpyAsync(m.d_refs.p, rf.data(), sizeof(float4) * S, cudaMemcpyHostToDevice, s));
         P2M_CUDA_TRY(cudaStreamSynchronize(s));
     }
-    // corner balls (Eq. 3 for vertex sites, Eq. 8 for auxiliary sites); a ball contained in
+    // corner balls (Eq. 3; for auxiliary sites with reference point proj(s, M), or Eq. 8's one
+    // enclosing ball when aux_balls = 0); a ball contained in
     // another ball of the same site adds nothing to the union and is dropped.  Sites are
     // independent: threads build each site's balls, which are then concatenated in order.
     m.ball_off.assign(S + 1, 0);
@@ -381,7 +382,9 @@ int build_partition(MeshData& m, const p2m_build_params& prm, p2m_index* h, cuda
             const int64_t c0 = ss.cell_off[i], c1 = ss.cell_off[i + 1];
             uc.clear();
             ur.clear();
-            if (m.site_kind[i] == 0) {
+            // a vertex site, or an auxiliary site with per-corner balls: Eq. 3 with reference
+            // point v (its vertex, or proj(s, M)); else the single Eq. 8 ball
+            if (m.site_kind[i] == 0 || prm.aux_balls) {
                 for (int64_t c = c0; c < c1; ++c) {
                     const double* u = &ss.cell_xyz[3 * c];
                     uc.insert(uc.end(), u, u + 3);
@@ -529,21 +532,7 @@ int build_partition(MeshData& m, const p2m_build_params& prm, p2m_index* h, cuda
             G = (int)std::lround(ext / (1.1 * spacing));
             G = std::max(8, std::min(G, 192));
         }
-        std::vector<float4> lo(S), hi(S);
-        for (int i = 0; i < S; ++i) {
-            lo[i] = make_float4(m.site_pos[3 * i], m.site_pos[3 * i + 1], m.site_pos[3 * i + 2], 0.f);
-            hi[i] = lo[i];
-        }
-        DevBuf dlo, dhi;
-        P2M_TRY(dlo.alloc(sizeof(float4) * S));
-        P2M_TRY(dhi.alloc(sizeof(float4) * S));
-        P2M_CUDA_TRY(cudaMemcpyAsync(dlo.p, lo.data(), sizeof(float4) * S, cudaMemcpyHostToDevice, s));
-        P2M_CUDA_TRY(cudaMemcpyAsync(dhi.p, hi.data(), sizeof(float4) * S, cudaMemcpyHostToDevice, s));
-        Bvh sb;
-        const float3 clo = make_float3((float)m.dom_lo[0], (float)m.dom_lo[1], (float)m.dom_lo[2]);
-        const float3 chi = make_float3((float)m.dom_hi[0], (float)m.dom_hi[1], (float)m.dom_hi[2]);
-        P2M_TRY(build_lbvh(dlo.as<float4>(), dhi.as<float4>(), S, clo, chi, sb, s));
-        P2M_TRY(build_grid(m, sb, G, status, s));
+        P2M_TRY(build_grid(m, ss, G, status, s));
         P2M_TRY(check_status_word(h, s, "nearest-site grid"));
         st.ms_grid = ms_now() - t6;
     }

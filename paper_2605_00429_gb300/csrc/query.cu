@@ -70,6 +70,200 @@ __global__ void __launch_bounds__(256, 6) k_query_thread(MeshView m, const float
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Site-staged schedule (5).  The queries are counting-sorted by their nearest site, so that
+// runs of consecutive queries share one interception list; a block of 256 queries stages the
+// short lists of its runs (entries, bounding spheres, full triangle records, chunk boxes) in
+// shared memory once, and every thread then scans its list from there.  The lanes of a warp
+// read the same staged entry at the same time (a broadcast), where the thread-per-query
+// kernels gather the same data through L1 once per lane.
+
+constexpr int kStage = 320;        // list entries one block stages
+constexpr int kStageChunks = 24;   // chunk boxes one block stages
+constexpr int kStageThreads = 256;
+
+// Pass 1, queries in input order: nearest site (K2) and the query's rank among the queries
+// of that site.  A point outside D gets the key n_sites.
+template <bool COUNT>
+__global__ void __launch_bounds__(256) k_site_rank(MeshView m, const float* __restrict__ pts, int64_t n,
+                                                  int* __restrict__ key, int* __restrict__ rank,
+                                                  int* __restrict__ count, unsigned long long* counters) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const float3 q = make_float3(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]);
+        int cell;
+        int site = -1;
+        if (grid_cell(m, q, cell)) site = nearest_site<COUNT>(m, q, cell, counters);
+        const int k = site >= 0 ? site : m.n_sites;
+        key[i] = k;
+        rank[i] = atomicAdd(count + k, 1);
+    }
+}
+
+// Pass 2: the points to their slots in site order, as (xyz, input index), with their site.
+__global__ void k_site_scatter(const float* __restrict__ pts, int64_t n, const int* __restrict__ key,
+                               const int* __restrict__ rank, const int* __restrict__ first, float4* __restrict__ qs,
+                               int* __restrict__ qsite) {
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int k = __ldg(key + i);
+        const int64_t slot = (int64_t)__ldg(first + k) + __ldg(rank + i);
+        qs[slot] = make_float4(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2], __int_as_float((int)i));
+        qsite[slot] = k;
+    }
+}
+
+// The record of a winner whose triangle record is already in registers.
+__device__ __forceinline__ void write_record_tri(const MeshView& m, float4* __restrict__ rec, int64_t i,
+                                                 unsigned long long key, float s, float t, const TriRec& T) {
+    const int f = (int)(key & 0xffffffffu);
+    const float3 p = tri_point(T, s, t);
+    rec[2 * i] = make_float4(sqrtf(__uint_as_float((unsigned)(key >> 32))), p.x, p.y, p.z);
+    rec[2 * i + 1] = make_float4(__int_as_float(__ldg(m.orig + f)), 1.0f - s - t, s, t);
+}
+
+// Pass 3: the list scan over the site-ordered queries, 256 per block iteration.
+template <bool COUNT>
+__global__ void __launch_bounds__(kStageThreads, 4)
+    k_query_staged(MeshView m, const float4* __restrict__ qs, const int* __restrict__ qsite, int64_t n,
+                   int32_t* __restrict__ rest, int* __restrict__ n_rest, int2* __restrict__ cand,
+                   unsigned char* __restrict__ flag, float4* __restrict__ rec, unsigned long long* counters) {
+    __shared__ int2 s_ent[kStage];
+    __shared__ float4 s_sph[kStage];
+    __shared__ float4 s_rec[kStage][4];
+    __shared__ float4 s_cb[kStageChunks][3];
+    __shared__ int s_site[kStageThreads];
+    __shared__ int s_wheads[kStageThreads / 32];
+    // runs of equal sites: site, list length, chunk count, staged entry offset (-1: not
+    // staged), staged chunk offset
+    __shared__ int s_run_site[kStageThreads], s_run_len[kStageThreads], s_run_nch[kStageThreads];
+    __shared__ int s_run_off[kStageThreads], s_run_coff[kStageThreads];
+    // staged runs only, in order: entry offset, first list position, chunk offset, first chunk
+    __shared__ int s_st_off[kStageThreads + 1], s_st_row[kStageThreads], s_st_coff[kStageThreads + 1],
+        s_st_gch[kStageThreads];
+    __shared__ int s_nruns, s_nstaged;
+    const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+    for (int64_t base = (int64_t)blockIdx.x * kStageThreads; base < n; base += (int64_t)gridDim.x * kStageThreads) {
+        const int64_t j = base + tid;
+        const bool valid = j < n;
+        const int site = valid ? __ldg(qsite + j) : -1;
+        s_site[tid] = site;
+        __syncthreads();
+        // run heads and run ids (inclusive count of heads up to this thread, minus one)
+        const bool head = valid && (tid == 0 || s_site[tid - 1] != site);
+        const unsigned hm = __ballot_sync(0xffffffffu, head);
+        if (lane == 0) s_wheads[wid] = __popc(hm);
+        __syncthreads();
+        int before = 0, total = 0;
+        for (int w = 0; w < kStageThreads / 32; ++w) {
+            before += w < wid ? s_wheads[w] : 0;
+            total += s_wheads[w];
+        }
+        const int run = before + __popc(hm & (0xffffffffu >> (31 - lane))) - 1;
+        if (head) {
+            s_run_site[run] = site;
+            int len = 0, nch = 0;
+            if (site < m.n_sites) {
+                len = __ldg(m.row_off + site + 1) - __ldg(m.row_off + site);
+                nch = __ldg(m.chunk_off + site + 1) - __ldg(m.chunk_off + site);
+            }
+            s_run_len[run] = len;
+            s_run_nch[run] = nch;
+        }
+        __syncthreads();
+        if (tid == 0) {
+            // stage whole short lists in run order while they fit
+            int cum = 0, ch = 0, k = 0;
+            for (int r = 0; r < total; ++r) {
+                const int st = s_run_site[r], len = s_run_len[r], nch = s_run_nch[r];
+                if (st < m.n_sites && len > 0 && len <= m.long_row && cum + len <= kStage && ch + nch <= kStageChunks) {
+                    s_run_off[r] = cum;
+                    s_run_coff[r] = ch;
+                    s_st_off[k] = cum;
+                    s_st_coff[k] = ch;
+                    s_st_row[k] = __ldg(m.row_off + st);
+                    s_st_gch[k] = __ldg(m.chunk_off + st);
+                    cum += len;
+                    ch += nch;
+                    ++k;
+                } else {
+                    s_run_off[r] = -1;
+                }
+            }
+            s_st_off[k] = cum;
+            s_st_coff[k] = ch;
+            s_nstaged = k;
+            s_nruns = total;
+        }
+        __syncthreads();
+        const int nst = s_nstaged, n_ent = s_st_off[nst], n_ch = s_st_coff[nst];
+        // cooperative staging: entry e belongs to the staged run whose range holds it
+        for (int e = tid; e < n_ent; e += kStageThreads) {
+            int lo = 0, hi = nst - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_st_off[mid] <= e) lo = mid;
+                else hi = mid - 1;
+            }
+            const int2 en = __ldg(m.row_ent + s_st_row[lo] + (e - s_st_off[lo]));
+            s_ent[e] = en;
+            s_sph[e] = __ldg(m.tsph + en.x);
+            const float4* tp = m.tri + 4 * (int64_t)en.x;
+            s_rec[e][0] = __ldg(tp);
+            s_rec[e][1] = __ldg(tp + 1);
+            s_rec[e][2] = __ldg(tp + 2);
+            s_rec[e][3] = __ldg(tp + 3);
+        }
+        for (int c = tid; c < n_ch; c += kStageThreads) {
+            int lo = 0, hi = nst - 1;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (s_st_coff[mid] <= c) lo = mid;
+                else hi = mid - 1;
+            }
+            const float4* r = m.cbox + 3 * ((int64_t)s_st_gch[lo] + (c - s_st_coff[lo]));
+            s_cb[c][0] = __ldg(r);
+            s_cb[c][1] = __ldg(r + 1);
+            s_cb[c][2] = __ldg(r + 2);
+        }
+        __syncthreads();
+        if (valid) {
+            const float4 p = __ldg(qs + j);
+            const int i = __float_as_int(p.w);
+            const float3 q = make_float3(p.x, p.y, p.z);
+            const bool inside = site < m.n_sites;
+            const int len = s_run_len[run];
+            const bool is_long = inside && len > m.long_row;
+            flag[j] = is_long;
+            cand[j] = make_int2(i, inside ? site : -1);
+            if (!is_long) {
+                unsigned long long key = ~0ull;
+                float bs = 0.0f, bt = 0.0f;
+                const int off = s_run_off[run];
+                if (inside && off >= 0) {
+                    int bpos = 0;
+                    key = scan_list_staged<COUNT>(m, q, site, s_ent + off, s_sph + off, s_rec + off,
+                                                  s_cb + s_run_coff[run], len, bs, bt, bpos, counters);
+                    if (key != ~0ull) {
+                        TriRec T;
+                        T.r0 = s_rec[off + bpos][0];
+                        T.r1 = s_rec[off + bpos][1];
+                        T.r2 = s_rec[off + bpos][2];
+                        T.r3 = s_rec[off + bpos][3];
+                        write_record_tri(m, rec, i, key, bs, bt, T);
+                    }
+                } else if (inside) {
+                    key = scan_list<COUNT>(m, q, site, bs, bt, counters);
+                    if (key != ~0ull) write_record(m, rec, i, key, bs, bt);
+                }
+                if (key == ~0ull) {
+                    rest[atomicAdd(n_rest, 1)] = i;
+                    if (COUNT) atomicAdd(counters + C_OUTSIDE, 1ull);
+                }
+            }
+        }
+        __syncthreads();  // the staged data and run tables are reused by the next iteration
+    }
+}
+
 // Batched path, after its radix sort: the points in sorted order with their index in .w,
 // so that the query kernels read them coalesced (the random gather runs here, in a
 // streaming kernel).
@@ -230,18 +424,19 @@ __device__ __forceinline__ unsigned spread8(unsigned v) {
 
 
 // Counting sort of the queries by the Morton code of their grid cell (mbits bits per axis,
-// G <= 2^mbits): each query takes its rank inside its cell from an atomic counter, an
+// G <= 2^mbits; the code shifted right by `shift` bits, i.e. the Morton code of a coarser
+// grid, when the call is small): each query takes its rank inside its cell from an atomic counter, an
 // exclusive scan of the counters gives each cell's first slot, and the points go straight to
 // their slots as (xyz, index).  Points outside the domain box get the last key and go last.
 // The order inside a cell is arbitrary; no result depends on it.
-__global__ void k_cell_rank(MeshView m, const float* __restrict__ pts, int64_t n, unsigned outside_key,
+__global__ void k_cell_rank(MeshView m, const float* __restrict__ pts, int64_t n, unsigned outside_key, int shift,
                             unsigned* __restrict__ key, int32_t* __restrict__ rank, int* __restrict__ count) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const float3 q = make_float3(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]);
         const float fx = (q.x - m.lo.x) * m.inv_h.x, fy = (q.y - m.lo.y) * m.inv_h.y, fz = (q.z - m.lo.z) * m.inv_h.z;
         unsigned k = outside_key;
         if (fx >= 0.0f && fy >= 0.0f && fz >= 0.0f && fx < (float)m.G && fy < (float)m.G && fz < (float)m.G)
-            k = (spread8((unsigned)fx) << 2) | (spread8((unsigned)fy) << 1) | spread8((unsigned)fz);
+            k = ((spread8((unsigned)fx) << 2) | (spread8((unsigned)fy) << 1) | spread8((unsigned)fz)) >> shift;
         key[i] = k;
         rank[i] = atomicAdd(count + k, 1);
     }
@@ -266,13 +461,81 @@ __global__ void k_site_only(MeshView m, const float* __restrict__ pts, int64_t n
 
 int query_grid_blocks(int64_t n, int threads) {
     const int64_t want = (n + threads - 1) / threads;
-    return (int)std::max<int64_t>(1, std::min<int64_t>(want, 152LL * 64));
+    return (int)std::max<int64_t>(1, std::min<int64_t>(want, (int64_t)sm_count() * 64));
+}
+
+// Site-staged schedule: nearest site + rank, scan, scatter into site order, staged scan,
+// compaction of the long-list queries, warp pass, record split, BVH pass for the rest.
+static int run_query_staged(p2m_index* h, MeshData& m, const float* d_pts, int64_t n, float* d_dist,
+                            float* d_closest, int32_t* d_tri, float* d_bary, unsigned long long* counters,
+                            DevBuf& rest, cudaStream_t s) {
+    const MeshView v = m.view();
+    const int S = v.n_sites;
+    auto up = [](size_t b) { return (b + 255) / 256 * 256; };
+    size_t scan_tmp = 0, sel_tmp = 0;
+    P2M_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, scan_tmp, (int*)nullptr, (int*)nullptr, S + 2, s));
+    P2M_CUDA_TRY(cub::DeviceSelect::Flagged(nullptr, sel_tmp, (int2*)nullptr, (unsigned char*)nullptr, (int2*)nullptr,
+                                            (int*)nullptr, (int)n, s));
+    const size_t a4 = up(sizeof(int) * n), a8 = up(sizeof(int2) * n), a16 = up(sizeof(float4) * n);
+    const size_t tmp_bytes = up(std::max(scan_tmp, sel_tmp)), site_bytes = up(sizeof(int) * (S + 2));
+    // rest ids, long queue, counters | key, rank, qsite | cand | flag | tmp | qs | rec | site count, first
+    const size_t total = a4 + a8 + 256 + 3 * a4 + a8 + up(n) + tmp_bytes + a16 + 2 * a16 + 2 * site_bytes;
+    P2M_TRY(rest.ensure(total));
+    char* p = rest.as<char>();
+    int32_t* d_rest = reinterpret_cast<int32_t*>(p); p += a4;
+    int2* d_long = reinterpret_cast<int2*>(p); p += a8;
+    int* d_cnt = reinterpret_cast<int*>(p); p += 256;  // [0] rest, [1] long, [2] head
+    int* key = reinterpret_cast<int*>(p); p += a4;
+    int* rank = reinterpret_cast<int*>(p); p += a4;
+    int* qsite = reinterpret_cast<int*>(p); p += a4;
+    int2* cand = reinterpret_cast<int2*>(p); p += a8;
+    unsigned char* flag = reinterpret_cast<unsigned char*>(p); p += up(n);
+    void* tmp = p; p += tmp_bytes;
+    float4* qs = reinterpret_cast<float4*>(p); p += a16;
+    float4* rec = reinterpret_cast<float4*>(p); p += 2 * a16;
+    int* site_count = reinterpret_cast<int*>(p); p += site_bytes;
+    int* site_first = reinterpret_cast<int*>(p);
+    P2M_CUDA_TRY(cudaMemsetAsync(d_cnt, 0, 4 * sizeof(int), s));
+    P2M_CUDA_TRY(cudaMemsetAsync(site_count, 0, sizeof(int) * (S + 2), s));
+    const int threads = 256;
+    const int blocks = query_grid_blocks(n, threads);
+    if (counters)
+        k_site_rank<true><<<blocks, threads, 0, s>>>(v, d_pts, n, key, rank, site_count, counters);
+    else
+        k_site_rank<false><<<blocks, threads, 0, s>>>(v, d_pts, n, key, rank, site_count, nullptr);
+    P2M_CUDA_TRY(cudaGetLastError());
+    P2M_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, scan_tmp, site_count, site_first, S + 2, s));
+    k_site_scatter<<<blocks, threads, 0, s>>>(d_pts, n, key, rank, site_first, qs, qsite);
+    P2M_CUDA_TRY(cudaGetLastError());
+    const int sblocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + kStageThreads - 1) / kStageThreads,
+                                                                    (int64_t)sm_count() * 32));
+    if (counters)
+        k_query_staged<true><<<sblocks, kStageThreads, 0, s>>>(v, qs, qsite, n, d_rest, d_cnt, cand, flag, rec, counters);
+    else
+        k_query_staged<false><<<sblocks, kStageThreads, 0, s>>>(v, qs, qsite, n, d_rest, d_cnt, cand, flag, rec, nullptr);
+    P2M_CUDA_TRY(cudaGetLastError());
+    // long-list queries, in site order (each block of the warp pass then works through one
+    // site's queries)
+    P2M_CUDA_TRY(cub::DeviceSelect::Flagged(tmp, sel_tmp, cand, flag, d_long, d_cnt + 1, (int)n, s));
+    const int wblocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, (int64_t)sm_count() * 16));
+    if (counters)
+        k_query_warp<true><<<wblocks, threads, 0, s>>>(v, d_pts, d_long, d_cnt + 1, d_dist, d_closest, d_tri, d_bary,
+                                                       d_rest, d_cnt, counters, d_cnt + 2, rec);
+    else
+        k_query_warp<false><<<wblocks, threads, 0, s>>>(v, d_pts, d_long, d_cnt + 1, d_dist, d_closest, d_tri, d_bary,
+                                                        d_rest, d_cnt, nullptr, d_cnt + 2, rec);
+    P2M_CUDA_TRY(cudaGetLastError());
+    k_split_records<<<blocks, threads, 0, s>>>(rec, n, d_dist, d_closest, d_tri, d_bary);
+    P2M_CUDA_TRY(cudaGetLastError());
+    return launch_bvh_closest(v, d_pts, d_rest, d_cnt, n, d_dist, d_closest, d_tri, d_bary, index_status(h), s);
 }
 
 int run_query(p2m_index* h, MeshData& m, const float* d_pts, int64_t n, float* d_dist, float* d_closest,
               int32_t* d_tri, float* d_bary, unsigned long long* counters, DevBuf& rest, cudaStream_t s) {
     const MeshView v = m.view();
     if (v.G == 0) return launch_bvh_closest(v, d_pts, nullptr, nullptr, n, d_dist, d_closest, d_tri, d_bary, index_status(h), s);
+    if (m.site_staged && n >= 4096)
+        return run_query_staged(h, m, d_pts, n, d_dist, d_closest, d_tri, d_bary, counters, rest, s);
     // scratch: rest ids [n], long queue [n] of int2, counters; for the sorted schedules also
     // the sort keys / permutation double buffers [4][n], per-query (query, site) pairs and long
     // flags, the temporary storage of the radix sorts and of the compaction, the points in
@@ -294,10 +557,14 @@ int run_query(p2m_index* h, MeshData& m, const float* d_pts, int64_t n, float* d
         P2M_CUDA_TRY(cub::DeviceSelect::Flagged(nullptr, sel_tmp, (int2*)nullptr, (unsigned char*)nullptr, (int2*)nullptr,
                                                 (int*)nullptr, (int)n, s));
     }
-    // counting sort over the Morton codes of the grid cells: mbits bits per axis
+    // counting sort over the Morton codes of the grid cells: mbits bits per axis, coarsened by
+    // `shift` bits per axis so that the key space (its counters are cleared and scanned on
+    // every call) stays within about 2n keys: small calls do not pay for a fine grid
     int mbits = 1;
     while ((1 << mbits) < v.G) ++mbits;
-    const int64_t n_keys = (int64_t)1 << (3 * mbits);  // key n_keys: outside the domain box
+    int shift = 0;
+    while (shift < mbits - 1 && ((int64_t)1 << (3 * (mbits - shift))) > std::max<int64_t>(2 * n, 4096)) ++shift;
+    const int64_t n_keys = (int64_t)1 << (3 * (mbits - shift));  // key n_keys: outside the domain box
     size_t scan_tmp = 0;
     if (sorted)
         P2M_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, scan_tmp, (int*)nullptr, (int*)nullptr, (int)(n_keys + 1), s));
@@ -314,7 +581,7 @@ int run_query(p2m_index* h, MeshData& m, const float* d_pts, int64_t n, float* d
     P2M_CUDA_TRY(cudaMemsetAsync(d_cnt, 0, 4 * sizeof(int), s));
     const int threads = 256;
     const int blocks = query_grid_blocks(n, threads);
-    const int wblocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, 152LL * 16));
+    const int wblocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, (int64_t)sm_count() * 16));
     int* head = nullptr;
     float4* rec = nullptr;
     if (sorted) {
@@ -338,7 +605,7 @@ int run_query(p2m_index* h, MeshData& m, const float* d_pts, int64_t n, float* d
         int* cell_first = reinterpret_cast<int*>(p + cell_bytes);
         // queries in grid-cell Morton order, gathered into qs (counting sort)
         P2M_CUDA_TRY(cudaMemsetAsync(cell_count, 0, sizeof(int) * (n_keys + 1), s));
-        k_cell_rank<<<blocks, threads, 0, s>>>(v, d_pts, n, (unsigned)n_keys, k0, i0, cell_count);
+        k_cell_rank<<<blocks, threads, 0, s>>>(v, d_pts, n, (unsigned)n_keys, 3 * shift, k0, i0, cell_count);
         P2M_CUDA_TRY(cudaGetLastError());
         P2M_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, scan_tmp, cell_count, cell_first, (int)(n_keys + 1), s));
         k_cell_scatter<<<blocks, threads, 0, s>>>(d_pts, n, k0, i0, cell_first, qs);
@@ -436,7 +703,7 @@ int launch_query_on_scratch(p2m_index* h, MeshData& m, const float* d_pts, int64
     P2M_CUDA_TRY(cudaMemsetAsync(d_cnt, 0, 2 * sizeof(int), s));
     const int threads = 256;
     const int blocks = query_grid_blocks(n, threads);
-    const int wblocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, 152LL * 16));
+    const int wblocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, (int64_t)sm_count() * 16));
     k_query_thread<false><<<blocks, threads, 0, s>>>(v, d_pts, n, d_dist, d_closest, d_tri, d_bary, d_rest, d_cnt, d_long,
                                                      d_cnt + 1, nullptr, nullptr, nullptr, nullptr, nullptr);
     k_query_warp<false><<<wblocks, threads, 0, s>>>(v, d_pts, d_long, d_cnt + 1, d_dist, d_closest, d_tri, d_bary, d_rest,

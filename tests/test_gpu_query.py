@@ -3,7 +3,8 @@ oracle, plus the structural checks that make the localised search exact:
 
 * K2 nearest site equals the brute-force nearest site over the index's own sites;
 * K1 list sandwich: for every site, {f : d(u,f) <= r_u - e} <= row <= {f : d(u,f) <= r_u + slack + e}
-  over its balls (brute force over all triangles);
+  over its balls (brute force over all triangles; the balls themselves are checked against
+  oracle cells in test_gpu_balls.py);
 * completeness: the oracle's closest triangle is in the list of the oracle's nearest site;
 * results: |d - d_oracle| <= 1e-6 diag, triangle id equal unless the oracle's two best are
   within that tolerance, closest point within 2e-6 diag, barycentrics consistent.
@@ -83,9 +84,6 @@ def check_structure(p2m, idx, mesh, q, n_sites_check=None, rng=None):
         may = set(np.nonzero(mg <= 2e-6 * mesh.diag() + eps)[0].tolist())
         assert must <= row, f"site {s}: {len(must - row)} triangles missing"
         assert row <= may, f"site {s}: {len(row - may)} extra triangles"
-    # Eq. 8 radius of auxiliary sites
-    for s in np.nonzero(kind == 1)[0][:50]:
-        assert boff[s + 1] - boff[s] == 1
     return ref
 
 
@@ -169,7 +167,7 @@ def test_counters(p2m):
     assert c["site_candidates"] >= 20000 - c["n_outside"]
 
 
-@pytest.mark.parametrize("schedule", [1, 2, 3, 4])
+@pytest.mark.parametrize("schedule", [1, 2, 3, 4, 5])
 def test_schedules_agree(p2m, schedule):
     """Thread-per-query, warp-per-query and the mixed schedule give the same answers."""
     mesh, q = W.workload_large(50_000, k=4)

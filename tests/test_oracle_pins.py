@@ -249,3 +249,64 @@ def test_signed_distance_sphere():
     r = np.linalg.norm(q.astype(np.float64), axis=1)
     far = np.abs(r - 1.0) > 0.01
     assert np.all(np.sign(sd[far]) == np.sign(r[far] - 1.0))
+
+
+def test_voronoi_cell_lattice_closed_form():
+    """Sites on a 4x4x4 lattice of spacing h: an interior site's cell is the cube of side h
+    centred on it, and a corner site's cell reaches the box corner."""
+    h = 0.25
+    g = (np.arange(4) + 0.5) * h
+    sites = np.array([[x, y, z] for z in g for y in g for x in g])
+    lo, hi = np.zeros(3), np.ones(3)
+    i = 1 + 4 * 1 + 16 * 2  # (1, 1, 2): interior
+    c = oracle.voronoi_cell(sites, i, lo, hi)
+    expect = {tuple(np.round(sites[i] + 0.5 * h * np.array([a, b, d]), 12)) for a in (-1, 1) for b in (-1, 1)
+              for d in (-1, 1)}
+    assert {tuple(np.round(u, 12)) for u in c} == expect
+    c0 = oracle.voronoi_cell(sites, 0, lo, hi)
+    assert {tuple(np.round(u, 12)) for u in c0} == {(x, y, z) for x in (0, h) for y in (0, h) for z in (0, h)}
+
+
+def test_voronoi_cell_two_sites_half_boxes():
+    s = np.array([[0.3, 0.5, 0.5], [0.7, 0.5, 0.5]])
+    c = oracle.voronoi_cell(s, 0, np.zeros(3), np.ones(3))
+    assert {tuple(np.round(u, 12)) for u in c} == {(x, y, z) for x in (0.0, 0.5) for y in (0.0, 1.0) for z in (0.0, 1.0)}
+
+
+def test_voronoi_cells_partition_the_box():
+    """Random sites: every corner lies in its closed cell (no other site strictly nearer) and
+    in D, and the cell volumes sum to vol(D)."""
+    from scipy.spatial import ConvexHull
+    rng = np.random.default_rng(11)
+    sites = rng.random((150, 3)) * np.array([2.0, 1.0, 0.5])
+    lo, hi = np.array([-0.1, -0.1, -0.1]), np.array([2.1, 1.1, 0.6])
+    vol = 0.0
+    for i in range(len(sites)):
+        c = oracle.voronoi_cell(sites, i, lo, hi)
+        d_own = np.linalg.norm(c - sites[i], axis=1)
+        d_all = np.min(np.linalg.norm(c[:, None, :] - sites[None, :, :], axis=2), axis=1)
+        assert np.all(d_own <= d_all + 1e-9)
+        assert np.all(c >= lo - 1e-12) and np.all(c <= hi + 1e-12)
+        vol += ConvexHull(c).volume
+    assert abs(vol - np.prod(hi - lo)) <= 1e-9 * np.prod(hi - lo)
+
+
+def test_vertex_sphere_union_theorem():
+    """Eq. 3 (Vertex Sphere Union): for a convex cell P with corners u and any fixed v, every
+    ball B(x, ||x - v||) with x in P lies inside the union of the corner balls B(u, ||u - v||).
+    Checked on random cells with random points of the small balls."""
+    rng = np.random.default_rng(12)
+    sites = rng.random((60, 3))
+    for i in range(10):
+        c = oracle.voronoi_cell(sites, i, np.zeros(3), np.ones(3))
+        v = rng.random(3) * 2 - 0.5
+        ru = np.linalg.norm(c - v, axis=1)
+        for _ in range(20):
+            w = rng.dirichlet(np.ones(len(c)))
+            x = w @ c
+            r = np.linalg.norm(x - v)
+            dirs = rng.normal(size=(200, 3))
+            dirs /= np.linalg.norm(dirs, axis=1)[:, None]
+            p = x + dirs * (r * rng.random(200) ** (1 / 3))[:, None]
+            cover = np.min(np.linalg.norm(p[:, None, :] - c[None, :, :], axis=2) - ru[None, :], axis=1)
+            assert np.all(cover <= 1e-12)

@@ -5,7 +5,9 @@ device memory in its own pool, a latency-bound loop, an operator hook that may n
 allocate); it runs the query kernels on a fixed scratch array inside the library.  This
 file runs last so that a failure here cannot hide the other tests; it also passes alone in
 a fresh process.  Two calls in a row must match p2m_query on the same index within the
-query tolerance (the scratch array keeps the previous call's contents)."""
+query tolerance (the scratch array keeps the previous call's contents).  The calls run with
+the library's host-side allocation fault injector armed (P2M_FAULT=alloc:1 makes the next
+device allocation fail), so any allocation on this path would fail the test."""
 import ctypes
 
 import numpy as np
@@ -17,7 +19,7 @@ import p2m_workloads as W
 pytestmark = pytest.mark.gpu
 
 
-def test_noalloc_matches_query_on_two_calls():
+def test_noalloc_matches_query_on_two_calls(monkeypatch):
     import torch
     from paper_2605_00429_gb300 import build as b
     b.build()
@@ -35,11 +37,15 @@ def test_noalloc_matches_query_on_two_calls():
         c = torch.empty(n, 3, device="cuda")
         t = torch.full((n,), -1, device="cuda", dtype=torch.int32)
         bb = torch.empty(n, 3, device="cuda")
+        torch.cuda.synchronize()
+        # armed injector: the first device allocation from here on fails with P2M_ERR_OOM
+        monkeypatch.setenv("P2M_FAULT", "alloc:1")
         rc = L.p2m_query_noalloc(idx._h, ctypes.c_void_p(pts.data_ptr()), n, ctypes.c_void_p(d.data_ptr()),
                                  ctypes.c_void_p(c.data_ptr()), ctypes.c_void_p(t.data_ptr()),
                                  ctypes.c_void_p(bb.data_ptr()), stream)
-        assert rc == 0, L.p2m_last_error()
         torch.cuda.synchronize()
+        monkeypatch.delenv("P2M_FAULT")
+        assert rc == 0, L.p2m_last_error()
         d, d_ref = d.cpu().numpy(), d_ref.cpu().numpy()
         assert np.max(np.abs(d.astype(np.float64) - d_ref)) <= tol, f"call {call}"
         ref = oracle.closest(mesh.verts, mesh.tris, part[:2000])
