@@ -209,6 +209,42 @@ def cpu_baseline(mesh, q, target_s=12.0, seed=0):
             "seconds": dt}
 
 
+def config_leg(p2m, key, dev, steps, schedule, flush, hbm_peak):
+    """One more workload of the contract, measured like the headline: build time, then the
+    query pass timed with CUDA events over `steps` steps (L2 flushed between steps)."""
+    import torch
+    desc, make = WORKLOADS[key]
+    mesh, q = make(0)
+    n = q.shape[0]
+    t0 = time.perf_counter()
+    idx = p2m.P2MIndex(mesh.verts, mesh.tris, schedule=schedule)
+    build_ms = (time.perf_counter() - t0) * 1e3
+    st = idx.stats()
+    pts = torch.from_numpy(q).to(dev)
+    out = (torch.empty(n, device=dev), torch.empty(n, 3, device=dev), torch.empty(n, device=dev, dtype=torch.int32),
+           torch.empty(n, 3, device=dev))
+    for _ in range(3):
+        idx.query(pts, out=out)
+    cnt = idx.counters(pts)
+    stream = torch.cuda.current_stream()
+    ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(steps)]
+    torch.cuda.synchronize()
+    for a, b in ev:
+        flush.zero_()
+        a.record(stream)
+        idx.query(pts, out=out)
+        b.record(stream)
+    torch.cuda.synchronize()
+    ms = float(np.mean([a.elapsed_time(b) for a, b in ev]))
+    del idx
+    return {"workload": desc, "queries": n, "tris": mesh.n_tris, "queries_per_s": n / (ms / 1e3), "ms_per_step": ms,
+            "steps": steps, "build_wall_ms": build_ms, "csr_build_ms": st["ms_tri"] + st["ms_lbvh"] + st["ms_k1"],
+            "grid_build_ms": st["ms_grid"], "sites": st["n_sites"], "aux_sites": st["n_aux_sites"],
+            "avg_list": st["avg_row"], "max_list": st["max_row"],
+            "queried_entries": cnt["row_entries"] / n, "queried_exact": cnt["exact_tests"] / n,
+            "hbm_frac": BYTES_PER_QUERY * n / (ms / 1e3) / 1e9 / hbm_peak}
+
+
 def run_reference(args, rank, world):
     """Reference arm: the FP64 oracle timed on the host cores, same metric."""
     if rank != 0:
@@ -298,7 +334,7 @@ def main():
     ap.add_argument("--queries", type=int, default=0, help="override the workload's query count")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-extras", action="store_true", help="skip fwd+bwd and e2e legs")
-    ap.add_argument("--schedule", type=int, default=0)
+    ap.add_argument("--schedule", type=int, default=5)
     ap.add_argument("--ablation", action="store_true", help="Table-4 style runs with / without site augmentation")
     ap.add_argument("--profile-range", action="store_true",
                     help="after the warm-up, run one query pass between cudaProfilerStart/Stop and exit "
@@ -406,10 +442,12 @@ def main():
             "build": {"wall_ms": build_wall_ms, "host_delaunay_ms": st["ms_delaunay"], "host_aug_ms": st["ms_aug"],
                       "gpu_cells_ms": st["ms_cells"], "cells_clipped_on_host": st["n_cells_host"], "gpu_lists_ms": st["ms_k1"], "gpu_grid_ms": st["ms_grid"],
                       "sites": st["n_sites"], "aux_sites": st["n_aux_sites"], "nnz": st["nnz"],
-                      "max_list": st["max_row"], "avg_list": st["avg_row"], "grid": st["grid_res"]},
+                      "max_list": st["max_row"], "avg_list": st["avg_row"], "grid": st["grid_res"],
+                      "grid_entries": st["grid_entries"], "grid_max": st["grid_max"]},
             "counters": {"queried_entries": cnt["row_entries"] / n, "queried_exact": cnt["exact_tests"] / n,
                          "sites_per_query": cnt["site_candidates"] / n, "outside": cnt["n_outside"],
-                         "tie_rechecks": cnt["tie_rechecks"]}}
+                         "tie_rechecks": cnt["tie_rechecks"], "long_queries": cnt["long_queries"],
+                         "long_entries_per_long_query": cnt["long_entries"] / max(1, cnt["long_queries"])}}
 
     if not args.no_extras:
         # end to end through the host-buffer C-ABI call: pinned inputs, all four outputs back
@@ -484,6 +522,15 @@ def main():
                          "workload": "256 noisy geodesic spheres / capped cylinders, T log-uniform [500, 200k], "
                                      "Q log-uniform [1k, 1M]; one persistent launch in a CUDA graph vs one launch per mesh"}
         del bidx, bpts, bout
+        # the other workloads of the contract, each on its own index, and the forward alone on
+        # the differentiation workload (beside fwd_bwd)
+        legs = {}
+        for key in ("small", "symmetric", "diff"):
+            if key == args.config:
+                continue
+            legs["diff_forward" if key == "diff" else key] = config_leg(
+                p2m, key, dev, max(3, min(args.steps, 20)), args.schedule, flush, float(pk.get("hbm_gbs", 6800.0)))
+        line["configs"] = legs
     else:
         line["e2e"] = None
 

@@ -81,26 +81,28 @@ typedef struct {
     float build_eps_rel;
     /* Nearest-site grid resolution per axis; 0 = automatic [0]. */
     int nn_grid_res;
-    /* Query schedule [0]: 0 = queries sorted by the Morton code of their grid cell, then
-     * thread per query for lists up to long_list entries and a warp-cooperative best-first
-     * scan for longer lists; 1 = thread per query for every list; 2 = warp per query for
-     * every list; 3 = as 0 without the sort; 4 = as 0, with the queries regrouped by
-     * nearest site (a second radix sort) before the list scan; 5 = queries counting-sorted
-     * by nearest site, each block of 256 staging its runs' short lists (entries, spheres,
-     * triangle records, chunk boxes) in shared memory before the scan, long lists as in 0.
-     * All give identical results. */
+    /* Query schedule [5]: 5 = queries counting-sorted by nearest site, then each block stages
+     * the short lists of the sites of its 1024 queries (entries, bounding spheres, triangle
+     * records, chunk boxes) in shared memory and scans them thread per query; lists longer
+     * than long_list take a warp-cooperative best-first scan (a call with fewer than 16
+     * queries per site takes schedule 0 instead); 0 = queries sorted by the Morton code of
+     * their grid cell, then thread per query for lists up to long_list entries and the
+     * warp-cooperative scan for longer lists; 1 = thread per query for every list; 2 = warp
+     * per query for every list; 3 = as 0 without the sort; 4 = as 0, with the queries
+     * regrouped by nearest site (a second radix sort) before the list scan.  All give
+     * identical results. */
     int schedule;
     /* Deterministic vertex-gradient accumulation (fixed-point integer atomics) [1]. */
     int deterministic;
     /* Seed of the site jitter used to break exact Delaunay degeneracies [1]. */
     int seed;
-    /* Lists longer than this take the warp-cooperative scan in schedules 0, 3 and 4; 0 picks
+    /* Lists longer than this take the warp-cooperative scan in schedules 0, 3, 4 and 5; 0 picks
      * the default (256) [0]. */
     int long_list;
     /* Clip the Voronoi cells on the GPU in FP64 [1]; cells beyond the device clipper's fixed
      * capacity (58 cutting planes) are clipped on the host.  0 = every cell on the host. */
     int gpu_cells;
-    /* Chunks of the host-buffer query pipeline (p2m_query_host); 0 picks the default (2) [0].
+    /* Chunks of the host-buffer query pipeline (p2m_query_host); 0 picks the default (3) [0].
      * More chunks overlap copies and compute better; fewer keep more queries per grid cell
      * in each chunk's Morton order. */
     int pipe_chunks;
@@ -145,6 +147,8 @@ typedef struct {
     int64_t tie_rechecks;     /* nearest-site decisions re-checked in FP64 */
     int64_t row_entries;      /* interception-list entries visited */
     int64_t exact_tests;      /* exact point-triangle tests run (after pruning) */
+    int64_t long_queries;     /* queries whose list was scanned by the warp-cooperative pass */
+    int64_t long_entries;     /* list entries those queries visited (part of row_entries) */
 } p2m_counters;
 
 /* Library version string. */
@@ -217,7 +221,7 @@ int p2m_mesh_distance_pair(p2m_index* a, p2m_index* b, int subdivisions, double*
 
 /* The same query from host memory: copies h_pts in chunks to the device, runs the query
  * and copies the results back.  Host buffers may be pageable, but pinned (cudaHostAlloc)
- * buffers are much faster: the chunks (pipe_chunks of the build parameters, 2 by default,
+ * buffers are much faster: the chunks (pipe_chunks of the build parameters, 3 by default,
  * at least 1M points each) run on separate streams, so one chunk's copies overlap another
  * chunk's kernels.  Output pointers other than h_dist may be NULL.  Synchronous: returns
  * when the outputs are in host memory.  Errors: INVALID_ARG, OOM, CUDA. */

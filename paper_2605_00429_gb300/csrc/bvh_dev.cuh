@@ -10,13 +10,18 @@ namespace p2m {
 constexpr int kBvhStack = 64;
 
 // Exact closest triangle of one query by branch and bound over the BVH.  Children are
-// visited nearer-first; a subtree is skipped only when its box is strictly farther than the
-// best squared distance found, so equal-distance triangles are still compared by id.
+// visited nearer-first; a subtree is skipped only when its box is farther than the bound
+// lim = d_best (1 + 9.6e-7) + slack, padded like the list scan's bound, so every triangle
+// whose distance rounds to the best is still compared by id and the result is the same
+// (distance, id) minimum the list scan finds.  bound0: a starting bound on d(q, M) (the
+// distance to a point of M, padded), or infinity.
 __device__ __forceinline__ unsigned long long bvh_closest_key(float3 q, const BNode* __restrict__ nodes, int root,
                                                               const float4* __restrict__ tri, float& bs, float& bt,
-                                                              unsigned* status) {
+                                                              unsigned* status, float bound0 = INFINITY,
+                                                              float slack = 0.0f) {
     unsigned long long best = ~0ull;
-    float best_d2 = INFINITY;
+    float lim = bound0;
+    float best_d2 = lim * lim;
     if (root < 0) {
         float s, t;
         const TriRec T = load_tri(tri, ~root);
@@ -45,7 +50,13 @@ __device__ __forceinline__ unsigned long long bvh_closest_key(float3 q, const BN
                 const TriRec T = load_tri(tri, ~c);
                 const float d2 = tri_dist2(q, T, s, t);
                 const unsigned long long key = dist_key(d2, ~c);
-                if (key < best) { best = key; best_d2 = d2; bs = s; bt = t; }
+                if (key < best) {
+                    best = key;
+                    bs = s;
+                    bt = t;
+                    lim = fminf(lim, fmaf(sqrtf(d2), 1.0f + 9.6e-7f, slack));
+                    best_d2 = lim * lim;
+                }
             } else if (next < 0) {
                 next = c;
             } else if (sp < kBvhStack) {

@@ -103,6 +103,7 @@ MeshView MeshData::view() const {
     v.long_row = long_row;
     v.cell_off = d_cell_off.as<const int32_t>();
     v.cell_site = d_cell_site.as<const float4>();
+    v.cell_id = d_cell_id.as<const int32_t>();
     v.G = G;
     v.lo = g_lo;
     v.hi = g_hi;
@@ -363,7 +364,7 @@ int p2m_default_params(p2m_build_params* out) {
     out->ring_radius_scale = 1.299038f;  // 0.75 * sqrt(3)
     out->build_eps_rel = 1e-6f;
     out->nn_grid_res = 0;
-    out->schedule = 0;
+    out->schedule = 5;
     out->deterministic = 1;
     out->seed = 1;
     out->gpu_cells = 1;
@@ -443,6 +444,8 @@ int p2m_query_counters(p2m_index* h, const float* d_pts, int64_t n, float* d_dis
     out->tie_rechecks = (int64_t)c[2];
     out->row_entries = (int64_t)c[3];
     out->exact_tests = (int64_t)c[4];
+    out->long_queries = (int64_t)c[5];
+    out->long_entries = (int64_t)c[6];
     return P2M_OK;
 }
 

@@ -5,13 +5,14 @@
 // nearest site's cell), so a query scans one short candidate list.
 //
 // The lists are built site by site, by rasterising each Voronoi cell into the grid.  A warp
-// takes one site s: starting from the grid-index box around the cell's corners, it splits
+// takes one site s (or one piece of the box of a large cell): starting from the grid-index
+// box around the cell's corners, it splits
 // boxes in two along their longest side and drops a box as soon as the whole box lies
 // strictly on the far side of the bisector between s and one of its Delaunay neighbours t
 // (every point of the box nearer to t than to s, so no point of cell(s) is in it).  Boxes of
 // one grid cell that survive are emitted as candidates.  Dropping uses one plane at a time,
-// and at most the 96 nearest neighbours' planes, so a box cut off only by two planes together
-// (or by a farther neighbour) survives: the lists may hold a few extra sites, never miss one.  Each grid cell is tested grown by 1% of a cell on every side, so a
+// and at most 96 neighbours' planes, so a box cut off only by two planes together (or by an
+// unused neighbour) survives: the lists may hold a few extra sites, never miss one.  Each grid cell is tested grown by 1% of a cell on every side, so a
 // query that FP32 rounding bins into a neighbouring cell still finds its nearest site.
 //
 // Count pass (cells' candidate counts, atomics), scan, fill pass (atomic slots), then each
@@ -59,23 +60,28 @@ __device__ __forceinline__ bool box_beyond(float3 bl, float3 bh, float4 p) {
     return 2.0f * (mx + my + mz) - p.w > 0.0f;
 }
 
-// Rasterise the Voronoi cells of sites [0, n_sites) into the grid.  FILL = false: count the
-// candidates of every grid cell (cell_count) and of every site (site_count).  FILL = true:
-// write each site into its grid cells' lists (out_site at cell_off[c] + an atomic slot).
+// Rasterise the Voronoi cells into the grid, one work item (site, box of grid indices) per
+// warp: a site whose box around its cell is large is cut into several items, so that no warp
+// walks a huge box alone.  FILL = false: count the candidates of every grid cell (cell_count)
+// and of every item (item_count).  FILL = true: write each site into its grid cells' lists
+// (out_site at cell_off[c] + an atomic slot).  nb_off / nb_id: the bisector neighbours of
+// each site used by the test (at most kRasterPlanes, see build_grid).
 template <bool FILL>
 __global__ void __launch_bounds__(32 * kRasterWarps)
-    k_grid_raster(RasterParams g, const float4* __restrict__ sites, int n_sites, const int64_t* __restrict__ nb_off,
-                  const int32_t* __restrict__ nb_id, const int4* __restrict__ root_box, int* __restrict__ cell_count,
-                  const int* __restrict__ cell_off, int* __restrict__ out_site, int* __restrict__ site_count,
-                  unsigned* status) {
+    k_grid_raster(RasterParams g, const float4* __restrict__ sites, const int32_t* __restrict__ nb_off,
+                  const int32_t* __restrict__ nb_id, const int4* __restrict__ items, int n_items,
+                  int* __restrict__ cell_count, const int* __restrict__ cell_off, int* __restrict__ out_site,
+                  int* __restrict__ item_count, unsigned* status) {
     __shared__ float4 planes[kRasterWarps][kRasterPlanes];
     __shared__ unsigned long long stack[kRasterWarps][kRasterStack];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const unsigned FULL = 0xffffffffu;
-    for (int s = blockIdx.x * kRasterWarps + w; s < n_sites; s += gridDim.x * kRasterWarps) {
+    for (int it = blockIdx.x * kRasterWarps + w; it < n_items; it += gridDim.x * kRasterWarps) {
+        const int4 item = __ldg(items + it);  // (site, x0 | x1 << 16, y0 | y1 << 16, z0 | z1 << 16)
+        const int s = item.x;
         const float4 sp = __ldg(sites + s);
-        const int64_t n0 = nb_off[s];
-        const int nn = (int)(nb_off[s + 1] - n0);
+        const int n0 = nb_off[s];
+        const int nn = nb_off[s + 1] - n0;
         // bisector of (s, t) relative to s: d = t - s (exact for lattice sites), |d|^2 and a
         // margin that covers the FP32 rounding of the test (|x'| <= the domain's extent)
         auto plane_of = [&](int k) {
@@ -84,9 +90,6 @@ __global__ void __launch_bounds__(32 * kRasterWarps)
             const float dd = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
             return make_float4(dx, dy, dz, dd + g.rel * fmaf(g.ext, sqrtf(dd), dd));
         };
-        // the nearest kRasterPlanes neighbours only (the lists are stored nearest first): a
-        // site with more neighbours (the centre of a co-spherical set has thousands) keeps a
-        // few extra grid cells but its rasterisation stays cheap
         const int np = min(nn, kRasterPlanes);
         __syncwarp();
         for (int k = lane; k < np; k += 32) planes[w][k] = plane_of(k);
@@ -109,13 +112,10 @@ __global__ void __launch_bounds__(32 * kRasterWarps)
             else atomicAdd(cell_count + c, 1);
             ++emitted;
         };
-        const int4 rb = __ldg(root_box + s);  // (x0 | x1 << 16, y0 | y1 << 16, z0 | z1 << 16, valid)
-        int sp_top = 0;
-        if (rb.w) {
-            if (lane == 0)
-                stack[w][0] = pack_box(rb.x & 0xffff, rb.x >> 16, rb.y & 0xffff, rb.y >> 16, rb.z & 0xffff, rb.z >> 16);
-            sp_top = 1;
-        }
+        if (lane == 0)
+            stack[w][0] = pack_box(item.y & 0xffff, item.y >> 16, item.z & 0xffff, item.z >> 16, item.w & 0xffff,
+                                   item.w >> 16);
+        int sp_top = 1;
         __syncwarp();
         while (sp_top > 0) {
             const int take = min(sp_top, 32);
@@ -164,8 +164,8 @@ __global__ void __launch_bounds__(32 * kRasterWarps)
         }
         for (int o = 16; o > 0; o >>= 1) emitted += __shfl_xor_sync(FULL, emitted, o);
         if (lane == 0) {
-            if (!FILL) site_count[s] = emitted;
-            else if (emitted != site_count[s]) atomicOr(status, ST_BAD);  // both passes walk alike
+            if (!FILL) item_count[it] = emitted;
+            else if (emitted != item_count[it]) atomicOr(status, ST_BAD);  // both passes walk alike
         }
     }
 }
@@ -198,57 +198,111 @@ int build_grid(MeshData& m, const SiteSet& ss, int G, unsigned* status, cudaStre
     ext = std::max(ext, m.diag);
     g.ext = (float)ext;
     g.rel = (float)std::ldexp(1.0, -14);
-    // the per-site root boxes (grid indices around the cell's corners, one cell of margin
-    // against rounding) and the neighbour CSR
-    std::vector<int4> rb(S);
+    // per site: the box of grid indices around its cell's corners (one cell of margin against
+    // rounding), cut into work items of at most kItemSide^3 grid cells; and the bisector
+    // neighbours the test uses.  A site with more than kRasterPlanes neighbours (the centre of
+    // a co-spherical or co-circular set has hundreds) keeps a subset spread over directions
+    // (farthest-point sampling of the unit vectors to them, starting from the nearest), so
+    // that its cell stays bounded on every side; fewer planes only add candidates.
+    constexpr int kItemSide = 24;
+    std::vector<std::vector<int4>> site_items(S);
+    std::vector<std::vector<int32_t>> site_nb(S);
     {
         std::atomic<int> next(0);
         auto work = [&]() {
+            std::vector<double> dir;
+            std::vector<double> mind;
             while (true) {
-                const int i0 = next.fetch_add(1024);
+                const int i0 = next.fetch_add(256);
                 if (i0 >= S) break;
-                for (int i = i0; i < std::min(S, i0 + 1024); ++i) {
+                for (int i = i0; i < std::min(S, i0 + 256); ++i) {
                     const int64_t c0 = ss.cell_off[i], c1 = ss.cell_off[i + 1];
-                    if (c1 <= c0) { rb[i] = make_int4(0, 0, 0, 0); continue; }
-                    double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
-                    for (int64_t c = c0; c < c1; ++c)
+                    if (c1 > c0) {
+                        double lo[3] = {1e300, 1e300, 1e300}, hi[3] = {-1e300, -1e300, -1e300};
+                        for (int64_t c = c0; c < c1; ++c)
+                            for (int k = 0; k < 3; ++k) {
+                                lo[k] = std::min(lo[k], ss.cell_xyz[3 * c + k]);
+                                hi[k] = std::max(hi[k], ss.cell_xyz[3 * c + k]);
+                            }
+                        int a[3], b[3];
                         for (int k = 0; k < 3; ++k) {
-                            lo[k] = std::min(lo[k], ss.cell_xyz[3 * c + k]);
-                            hi[k] = std::max(hi[k], ss.cell_xyz[3 * c + k]);
+                            const double hk = (m.dom_hi[k] - m.dom_lo[k]) / G;
+                            a[k] = std::max(0, std::min(G - 1, (int)std::floor((lo[k] - m.dom_lo[k]) / hk) - 1));
+                            b[k] = std::max(0, std::min(G - 1, (int)std::floor((hi[k] - m.dom_lo[k]) / hk) + 1));
                         }
-                    int a[3], b[3];
-                    for (int k = 0; k < 3; ++k) {
-                        const double hk = (m.dom_hi[k] - m.dom_lo[k]) / G;
-                        a[k] = (int)std::floor((lo[k] - m.dom_lo[k]) / hk) - 1;
-                        b[k] = (int)std::floor((hi[k] - m.dom_lo[k]) / hk) + 1;
-                        a[k] = std::max(0, std::min(G - 1, a[k]));
-                        b[k] = std::max(0, std::min(G - 1, b[k]));
+                        for (int z = a[2]; z <= b[2]; z += kItemSide)
+                            for (int y = a[1]; y <= b[1]; y += kItemSide)
+                                for (int x = a[0]; x <= b[0]; x += kItemSide) {
+                                    const int x1 = std::min(b[0], x + kItemSide - 1), y1 = std::min(b[1], y + kItemSide - 1),
+                                              z1 = std::min(b[2], z + kItemSide - 1);
+                                    site_items[i].push_back(make_int4(i, x | (x1 << 16), y | (y1 << 16), z | (z1 << 16)));
+                                }
                     }
-                    rb[i] = make_int4(a[0] | (b[0] << 16), a[1] | (b[1] << 16), a[2] | (b[2] << 16), 1);
+                    const int64_t n0 = ss.nb_off[i], nn = ss.nb_off[i + 1] - n0;
+                    std::vector<int32_t>& out = site_nb[i];
+                    if (nn <= kRasterPlanes) {
+                        out.assign(ss.nb_id.begin() + n0, ss.nb_id.begin() + n0 + nn);
+                        continue;
+                    }
+                    const float* ps = m.site_pos.data();
+                    dir.assign(3 * nn, 0.0);
+                    for (int64_t k = 0; k < nn; ++k) {
+                        const int t = ss.nb_id[n0 + k];
+                        double d[3], l = 0;
+                        for (int c = 0; c < 3; ++c) {
+                            d[c] = (double)ps[3 * t + c] - (double)ps[3 * i + c];
+                            l += d[c] * d[c];
+                        }
+                        l = std::sqrt(std::max(l, 1e-300));
+                        for (int c = 0; c < 3; ++c) dir[3 * k + c] = d[c] / l;
+                    }
+                    mind.assign(nn, 1e300);
+                    int64_t pick = 0;  // the nearest neighbour (lists are nearest first)
+                    for (int r = 0; r < kRasterPlanes; ++r) {
+                        out.push_back(ss.nb_id[n0 + pick]);
+                        int64_t far = -1;
+                        for (int64_t k = 0; k < nn; ++k) {
+                            const double dd = 1.0 - (dir[3 * k] * dir[3 * pick] + dir[3 * k + 1] * dir[3 * pick + 1] +
+                                                     dir[3 * k + 2] * dir[3 * pick + 2]);
+                            mind[k] = std::min(mind[k], dd);
+                            if (mind[k] > 0 && (far < 0 || mind[k] > mind[far])) far = k;
+                        }
+                        if (far < 0) break;
+                        pick = far;
+                    }
                 }
             }
         };
         std::vector<std::thread> th;
-        for (int t = 0; t < std::max(1, std::min(hardware_threads(), (S + 1023) / 1024)); ++t) th.emplace_back(work);
+        for (int t = 0; t < std::max(1, std::min(hardware_threads(), (S + 255) / 256)); ++t) th.emplace_back(work);
         for (auto& t : th) t.join();
     }
-    const int64_t nnb = ss.nb_off[S];
-    DevBuf d_rb, d_nboff, d_nb, d_count, d_off, d_site_count, d_ids, d_ids2, tmp;
-    P2M_TRY(d_rb.alloc(sizeof(int4) * S));
-    P2M_TRY(d_nboff.alloc(sizeof(int64_t) * (S + 1)));
-    P2M_TRY(d_nb.alloc(sizeof(int32_t) * std::max<int64_t>(nnb, 1)));
+    std::vector<int4> items;
+    std::vector<int32_t> rnb_off(S + 1, 0), rnb;
+    for (int i = 0; i < S; ++i) {
+        items.insert(items.end(), site_items[i].begin(), site_items[i].end());
+        rnb.insert(rnb.end(), site_nb[i].begin(), site_nb[i].end());
+        rnb_off[i + 1] = (int32_t)rnb.size();
+    }
+    const int n_items = (int)items.size();
+    DevBuf d_items, d_nboff, d_nb, d_count, d_off, d_item_count, d_ids, d_ids2, tmp;
+    P2M_TRY(d_items.alloc(sizeof(int4) * std::max(n_items, 1)));
+    P2M_TRY(d_nboff.alloc(sizeof(int32_t) * (S + 1)));
+    P2M_TRY(d_nb.alloc(sizeof(int32_t) * std::max<size_t>(rnb.size(), 1)));
     P2M_TRY(d_count.alloc(sizeof(int) * (n_cells + 1)));
     P2M_TRY(d_off.alloc(sizeof(int) * (n_cells + 1)));
-    P2M_TRY(d_site_count.alloc(sizeof(int) * S));
-    P2M_CUDA_TRY(cudaMemcpyAsync(d_rb.p, rb.data(), sizeof(int4) * S, cudaMemcpyHostToDevice, s));
-    P2M_CUDA_TRY(cudaMemcpyAsync(d_nboff.p, ss.nb_off.data(), sizeof(int64_t) * (S + 1), cudaMemcpyHostToDevice, s));
-    if (nnb > 0) P2M_CUDA_TRY(cudaMemcpyAsync(d_nb.p, ss.nb_id.data(), sizeof(int32_t) * nnb, cudaMemcpyHostToDevice, s));
+    P2M_TRY(d_item_count.alloc(sizeof(int) * std::max(n_items, 1)));
+    if (n_items > 0)
+        P2M_CUDA_TRY(cudaMemcpyAsync(d_items.p, items.data(), sizeof(int4) * n_items, cudaMemcpyHostToDevice, s));
+    P2M_CUDA_TRY(cudaMemcpyAsync(d_nboff.p, rnb_off.data(), sizeof(int32_t) * (S + 1), cudaMemcpyHostToDevice, s));
+    if (!rnb.empty())
+        P2M_CUDA_TRY(cudaMemcpyAsync(d_nb.p, rnb.data(), sizeof(int32_t) * rnb.size(), cudaMemcpyHostToDevice, s));
     P2M_CUDA_TRY(cudaMemsetAsync(d_count.p, 0, sizeof(int) * (n_cells + 1), s));
-    const int blocks = std::max(1, std::min((S + kRasterWarps - 1) / kRasterWarps, sm_count() * 16));
+    const int blocks = std::max(1, std::min((n_items + kRasterWarps - 1) / kRasterWarps, sm_count() * 16));
     const float4* sites = m.d_sites.as<float4>();
-    k_grid_raster<false><<<blocks, 32 * kRasterWarps, 0, s>>>(g, sites, S, d_nboff.as<int64_t>(), d_nb.as<int32_t>(),
-                                                               d_rb.as<int4>(), d_count.as<int>(), nullptr, nullptr,
-                                                               d_site_count.as<int>(), status);
+    k_grid_raster<false><<<blocks, 32 * kRasterWarps, 0, s>>>(g, sites, d_nboff.as<int32_t>(), d_nb.as<int32_t>(),
+                                                               d_items.as<int4>(), n_items, d_count.as<int>(), nullptr,
+                                                               nullptr, d_item_count.as<int>(), status);
     P2M_CUDA_TRY(cudaGetLastError());
     size_t tb = 0, tb2 = 0;
     P2M_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, tb, d_count.as<int>(), d_off.as<int>(), (int)(n_cells + 1), s));
@@ -269,9 +323,10 @@ int build_grid(MeshData& m, const SiteSet& ss, int G, unsigned* status, cudaStre
     P2M_TRY(d_ids.alloc(sizeof(int) * std::max<int64_t>(total, 1)));
     P2M_TRY(d_ids2.alloc(sizeof(int) * std::max<int64_t>(total, 1)));
     P2M_CUDA_TRY(cudaMemsetAsync(d_count.p, 0, sizeof(int) * (n_cells + 1), s));
-    k_grid_raster<true><<<blocks, 32 * kRasterWarps, 0, s>>>(g, sites, S, d_nboff.as<int64_t>(), d_nb.as<int32_t>(),
-                                                              d_rb.as<int4>(), d_count.as<int>(), d_off.as<int>(),
-                                                              d_ids.as<int>(), d_site_count.as<int>(), status);
+    k_grid_raster<true><<<blocks, 32 * kRasterWarps, 0, s>>>(g, sites, d_nboff.as<int32_t>(), d_nb.as<int32_t>(),
+                                                              d_items.as<int4>(), n_items, d_count.as<int>(),
+                                                              d_off.as<int>(), d_ids.as<int>(), d_item_count.as<int>(),
+                                                              status);
     P2M_CUDA_TRY(cudaGetLastError());
     if (total > 0)
         P2M_CUDA_TRY(cub::DeviceSegmentedSort::SortKeys(tmp.p, tb2, d_ids.as<int>(), d_ids2.as<int>(), (int)total,
@@ -283,6 +338,7 @@ int build_grid(MeshData& m, const SiteSet& ss, int G, unsigned* status, cudaStre
         P2M_CUDA_TRY(cudaGetLastError());
     }
     m.d_cell_off = std::move(d_off);
+    m.d_cell_id = std::move(d_ids2);
     P2M_CUDA_TRY(cudaStreamSynchronize(s));
     m.G = G;
     m.g_lo = g.lo;

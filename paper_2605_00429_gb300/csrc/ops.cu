@@ -339,7 +339,7 @@ int p2m_query_host(p2m_index* h, const float* h_pts, int64_t n, float* h_dist, f
     // Two chunks by default: a chunk's Morton order only groups its own points, so smaller
     // chunks put fewer queries in each grid cell and cost more per query (10M points in
     // 1 / 2 / 4 / 8 chunks: 4.73 / 3.86 / 4.04 / 4.64 ms end to end).
-    const int64_t k_chunks = h->params.pipe_chunks > 0 ? h->params.pipe_chunks : 2;
+    const int64_t k_chunks = h->params.pipe_chunks > 0 ? h->params.pipe_chunks : 3;
     const int64_t chunk = std::min<int64_t>(n, std::max<int64_t>((int64_t)1 << 20, (n + k_chunks - 1) / k_chunks));
     for (int k = 0; k < kSlots; ++k) {
         P2M_TRY(h->pipe[k][0].ensure(sizeof(float) * 3 * chunk));

@@ -105,6 +105,7 @@ struct MeshView {
     const float4* l1box;    // [n_l1][2]
     const int32_t* cell_off;// [G^3+1] nearest-site grid CSR
     const float4* cell_site;// candidates: (x, y, z, site id as int bits)
+    const int32_t* cell_id; // the same candidates as site ids (4 B each; positions from `sites`)
     int G;                  // grid cells per axis (0 => no grid: every query takes the BVH path)
     float3 lo;              // domain D lower corner
     float3 inv_h;           // 1 / grid cell size
@@ -134,7 +135,7 @@ struct MeshData {
     DevBuf d_snorm, d_vnorm;     // pseudonormals for the sign: [T][4] (face, edges 01/12/20), [V]
     std::vector<int32_t> orig;   // host copy of d_orig
     Bvh bvh;
-    DevBuf d_sites, d_refs, d_row_off, d_row_tri, d_row_key, d_row_ent, d_cell_off, d_cell_site, d_chunk_off, d_cbox, d_l1_off, d_l1box;
+    DevBuf d_sites, d_refs, d_row_off, d_row_tri, d_row_key, d_row_ent, d_cell_off, d_cell_site, d_cell_id, d_chunk_off, d_cbox, d_l1_off, d_l1box;
     int64_t nnz = 0, n_chunks = 0;
     int long_row = 256;
     bool sorted = true;          // process queries in grid-cell Morton order

@@ -78,9 +78,12 @@ __global__ void __launch_bounds__(256, 6) k_query_thread(MeshView m, const float
 // read the same staged entry at the same time (a broadcast), where the thread-per-query
 // kernels gather the same data through L1 once per lane.
 
-constexpr int kStage = 320;        // list entries one block stages
-constexpr int kStageChunks = 24;   // chunk boxes one block stages
+constexpr int kStage = 448;        // list entries one block stages
+constexpr int kStageChunks = 32;   // chunk boxes one block stages
 constexpr int kStageThreads = 256;
+constexpr int kStagePer = 4;       // queries per thread in one block iteration
+constexpr int kStageTile = kStageThreads * kStagePer;
+constexpr int kStageRuns = 64;     // runs (sites) one tile may span; the rest scan unstaged
 
 // Pass 1, queries in input order: nearest site (K2) and the query's rank among the queries
 // of that site.  A point outside D gets the key n_sites.
@@ -92,22 +95,20 @@ __global__ void __launch_bounds__(256) k_site_rank(MeshView m, const float* __re
         const float3 q = make_float3(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]);
         int cell;
         int site = -1;
-        if (grid_cell(m, q, cell)) site = nearest_site<COUNT>(m, q, cell, counters);
+        if (grid_cell(m, q, cell)) site = nearest_site<COUNT, true>(m, q, cell, counters);
         const int k = site >= 0 ? site : m.n_sites;
         key[i] = k;
         rank[i] = atomicAdd(count + k, 1);
     }
 }
 
-// Pass 2: the points to their slots in site order, as (xyz, input index), with their site.
+// Pass 2: the points to their slots in site order, as (xyz, input index).
 __global__ void k_site_scatter(const float* __restrict__ pts, int64_t n, const int* __restrict__ key,
-                               const int* __restrict__ rank, const int* __restrict__ first, float4* __restrict__ qs,
-                               int* __restrict__ qsite) {
+                               const int* __restrict__ rank, const int* __restrict__ first, float4* __restrict__ qs) {
     for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
         const int k = __ldg(key + i);
         const int64_t slot = (int64_t)__ldg(first + k) + __ldg(rank + i);
         qs[slot] = make_float4(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2], __int_as_float((int)i));
-        qsite[slot] = k;
     }
 }
 
@@ -120,67 +121,92 @@ __device__ __forceinline__ void write_record_tri(const MeshView& m, float4* __re
     rec[2 * i + 1] = make_float4(__int_as_float(__ldg(m.orig + f)), 1.0f - s - t, s, t);
 }
 
-// Pass 3: the list scan over the site-ordered queries, 256 per block iteration.
+// Pass 3: the list scan over the site-ordered queries, kStageTile per block iteration.  The
+// tile's runs (sites) come from the site offsets `first` (first[s] = the first slot of site
+// s, first[n_sites + 1] = n; key n_sites = outside D): a binary search finds the site of the
+// tile's first query, and the next offsets give the runs.  Whole short lists of the runs are
+// staged while they fit; each thread then scans kStagePer queries (lanes of a warp take
+// consecutive queries, mostly of one site, so their reads of the staged list are broadcasts).
 template <bool COUNT>
 __global__ void __launch_bounds__(kStageThreads, 4)
-    k_query_staged(MeshView m, const float4* __restrict__ qs, const int* __restrict__ qsite, int64_t n,
-                   int32_t* __restrict__ rest, int* __restrict__ n_rest, int2* __restrict__ cand,
-                   unsigned char* __restrict__ flag, float4* __restrict__ rec, unsigned long long* counters) {
+    k_query_staged(MeshView m, const float4* __restrict__ qs, const int* __restrict__ first, int64_t n,
+                   int32_t* __restrict__ rest, int* __restrict__ n_rest, int2* __restrict__ longq,
+                   int* __restrict__ n_long, float4* __restrict__ rec, unsigned long long* counters) {
     __shared__ int2 s_ent[kStage];
     __shared__ float4 s_sph[kStage];
     __shared__ float4 s_rec[kStage][4];
     __shared__ float4 s_cb[kStageChunks][3];
-    __shared__ int s_site[kStageThreads];
-    __shared__ int s_wheads[kStageThreads / 32];
-    // runs of equal sites: site, list length, chunk count, staged entry offset (-1: not
-    // staged), staged chunk offset
-    __shared__ int s_run_site[kStageThreads], s_run_len[kStageThreads], s_run_nch[kStageThreads];
-    __shared__ int s_run_off[kStageThreads], s_run_coff[kStageThreads];
-    // staged runs only, in order: entry offset, first list position, chunk offset, first chunk
-    __shared__ int s_st_off[kStageThreads + 1], s_st_row[kStageThreads], s_st_coff[kStageThreads + 1],
-        s_st_gch[kStageThreads];
-    __shared__ int s_nruns, s_nstaged;
+    // runs: site, first slot, list start / length, chunk start / count, staged entry and
+    // chunk offsets (-1: not staged)
+    __shared__ int s_run_site[kStageRuns], s_run_beg[kStageRuns + 1];
+    __shared__ int s_run_row[kStageRuns], s_run_len[kStageRuns], s_run_gch[kStageRuns], s_run_nch[kStageRuns];
+    __shared__ int s_run_off[kStageRuns], s_run_coff[kStageRuns];
+    __shared__ int s_st_run[kStageRuns], s_st_off[kStageRuns + 1], s_st_coff[kStageRuns + 1];
+    __shared__ int s_nruns, s_nstaged, s_site0;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-    for (int64_t base = (int64_t)blockIdx.x * kStageThreads; base < n; base += (int64_t)gridDim.x * kStageThreads) {
-        const int64_t j = base + tid;
-        const bool valid = j < n;
-        const int site = valid ? __ldg(qsite + j) : -1;
-        s_site[tid] = site;
-        __syncthreads();
-        // run heads and run ids (inclusive count of heads up to this thread, minus one)
-        const bool head = valid && (tid == 0 || s_site[tid - 1] != site);
-        const unsigned hm = __ballot_sync(0xffffffffu, head);
-        if (lane == 0) s_wheads[wid] = __popc(hm);
-        __syncthreads();
-        int before = 0, total = 0;
-        for (int w = 0; w < kStageThreads / 32; ++w) {
-            before += w < wid ? s_wheads[w] : 0;
-            total += s_wheads[w];
-        }
-        const int run = before + __popc(hm & (0xffffffffu >> (31 - lane))) - 1;
-        if (head) {
-            s_run_site[run] = site;
-            int len = 0, nch = 0;
-            if (site < m.n_sites) {
-                len = __ldg(m.row_off + site + 1) - __ldg(m.row_off + site);
-                nch = __ldg(m.chunk_off + site + 1) - __ldg(m.chunk_off + site);
+    const int S = m.n_sites;
+    for (int64_t base = (int64_t)blockIdx.x * kStageTile; base < n; base += (int64_t)gridDim.x * kStageTile) {
+        const int64_t tend = min(base + (int64_t)kStageTile, n);
+        if (tid == 0) {
+            // the site of the tile's first query: the last s in [0, S] with first[s] <= base
+            int lo = 0, hi = S;
+            while (lo < hi) {
+                const int mid = (lo + hi + 1) >> 1;
+                if (__ldg(first + mid) <= base) lo = mid;
+                else hi = mid - 1;
             }
-            s_run_len[run] = len;
-            s_run_nch[run] = nch;
+            s_site0 = lo;
+        }
+        __syncthreads();
+        if (wid == 0) {
+            // runs: sites s0, s0 + 1, ... with queries in [base, tend), 32 offsets per step
+            int nr = 0, s = s_site0;
+            while (nr < kStageRuns && s <= S) {
+                const int ss = s + lane;
+                const int f0 = ss <= S ? __ldg(first + ss) : (int)n;
+                const int f1 = ss <= S ? __ldg(first + ss + 1) : (int)n;
+                const bool has = ss <= S && f1 > f0 && f0 < tend && f1 > base;
+                const unsigned hm = __ballot_sync(0xffffffffu, has);
+                const int r = nr + __popc(hm & ((1u << lane) - 1u));
+                if (has && r < kStageRuns) {
+                    s_run_site[r] = ss;
+                    s_run_beg[r] = (int)max((int64_t)f0, base);
+                }
+                nr = min(kStageRuns, nr + __popc(hm));
+                const bool past = ss > S || f0 >= tend;
+                if (__any_sync(0xffffffffu, past)) break;
+                s += 32;
+            }
+            if (lane == 0) s_nruns = nr;
+        }
+        __syncthreads();
+        const int nr = s_nruns;
+        if (tid < nr) {
+            const int st = s_run_site[tid];
+            int r0 = 0, len = 0, g0 = 0, nch = 0;
+            if (st < S) {
+                r0 = __ldg(m.row_off + st);
+                len = __ldg(m.row_off + st + 1) - r0;
+                g0 = __ldg(m.chunk_off + st);
+                nch = __ldg(m.chunk_off + st + 1) - g0;
+            }
+            s_run_row[tid] = r0;
+            s_run_len[tid] = len;
+            s_run_gch[tid] = g0;
+            s_run_nch[tid] = nch;
         }
         __syncthreads();
         if (tid == 0) {
             // stage whole short lists in run order while they fit
             int cum = 0, ch = 0, k = 0;
-            for (int r = 0; r < total; ++r) {
-                const int st = s_run_site[r], len = s_run_len[r], nch = s_run_nch[r];
-                if (st < m.n_sites && len > 0 && len <= m.long_row && cum + len <= kStage && ch + nch <= kStageChunks) {
+            for (int r = 0; r < nr; ++r) {
+                const int len = s_run_len[r], nch = s_run_nch[r];
+                if (s_run_site[r] < S && len > 0 && len <= m.long_row && cum + len <= kStage && ch + nch <= kStageChunks) {
                     s_run_off[r] = cum;
                     s_run_coff[r] = ch;
+                    s_st_run[k] = r;
                     s_st_off[k] = cum;
                     s_st_coff[k] = ch;
-                    s_st_row[k] = __ldg(m.row_off + st);
-                    s_st_gch[k] = __ldg(m.chunk_off + st);
                     cum += len;
                     ch += nch;
                     ++k;
@@ -191,11 +217,12 @@ __global__ void __launch_bounds__(kStageThreads, 4)
             s_st_off[k] = cum;
             s_st_coff[k] = ch;
             s_nstaged = k;
-            s_nruns = total;
+            // queries past the last run (a tile spanning more than kStageRuns sites) scan
+            // unstaged; mark where the runs end
+            s_run_beg[nr] = nr < kStageRuns ? (int)tend : s_run_beg[nr - 1];
         }
         __syncthreads();
         const int nst = s_nstaged, n_ent = s_st_off[nst], n_ch = s_st_coff[nst];
-        // cooperative staging: entry e belongs to the staged run whose range holds it
         for (int e = tid; e < n_ent; e += kStageThreads) {
             int lo = 0, hi = nst - 1;
             while (lo < hi) {
@@ -203,7 +230,7 @@ __global__ void __launch_bounds__(kStageThreads, 4)
                 if (s_st_off[mid] <= e) lo = mid;
                 else hi = mid - 1;
             }
-            const int2 en = __ldg(m.row_ent + s_st_row[lo] + (e - s_st_off[lo]));
+            const int2 en = __ldg(m.row_ent + s_run_row[s_st_run[lo]] + (e - s_st_off[lo]));
             s_ent[e] = en;
             s_sph[e] = __ldg(m.tsph + en.x);
             const float4* tp = m.tri + 4 * (int64_t)en.x;
@@ -219,45 +246,83 @@ __global__ void __launch_bounds__(kStageThreads, 4)
                 if (s_st_coff[mid] <= c) lo = mid;
                 else hi = mid - 1;
             }
-            const float4* r = m.cbox + 3 * ((int64_t)s_st_gch[lo] + (c - s_st_coff[lo]));
+            const float4* r = m.cbox + 3 * ((int64_t)s_run_gch[s_st_run[lo]] + (c - s_st_coff[lo]));
             s_cb[c][0] = __ldg(r);
             s_cb[c][1] = __ldg(r + 1);
             s_cb[c][2] = __ldg(r + 2);
         }
         __syncthreads();
-        if (valid) {
-            const float4 p = __ldg(qs + j);
+        for (int k = 0; k < kStagePer; ++k) {
+            if (base + k * kStageThreads >= tend) break;  // uniform over the block
+            const int64_t j = base + k * kStageThreads + tid;
+            const bool valid = j < tend;
+            // the run holding slot j (runs are in slot order)
+            int run = -1;
+            if (valid && nr > 0 && j < s_run_beg[nr]) {
+                int lo = 0, hi = nr - 1;
+                while (lo < hi) {
+                    const int mid = (lo + hi + 1) >> 1;
+                    if (s_run_beg[mid] <= j) lo = mid;
+                    else hi = mid - 1;
+                }
+                run = lo;
+            }
+            float4 p = make_float4(0.f, 0.f, 0.f, 0.f);
+            int site = S;
+            if (valid) {
+                p = __ldg(qs + j);
+                if (run >= 0) {
+                    site = s_run_site[run];
+                } else {
+                    // beyond the tile's run table: find the site by binary search of the offsets
+                    int lo = 0, hi = S;
+                    while (lo < hi) {
+                        const int mid = (lo + hi + 1) >> 1;
+                        if (__ldg(first + mid) <= j) lo = mid;
+                        else hi = mid - 1;
+                    }
+                    site = lo;
+                }
+            }
             const int i = __float_as_int(p.w);
             const float3 q = make_float3(p.x, p.y, p.z);
-            const bool inside = site < m.n_sites;
-            const int len = s_run_len[run];
+            const bool inside = valid && site < S;
+            const int len = inside ? (run >= 0 ? s_run_len[run] : __ldg(m.row_off + site + 1) - __ldg(m.row_off + site)) : 0;
             const bool is_long = inside && len > m.long_row;
-            flag[j] = is_long;
-            cand[j] = make_int2(i, inside ? site : -1);
-            if (!is_long) {
-                unsigned long long key = ~0ull;
-                float bs = 0.0f, bt = 0.0f;
-                const int off = s_run_off[run];
-                if (inside && off >= 0) {
-                    int bpos = 0;
-                    key = scan_list_staged<COUNT>(m, q, site, s_ent + off, s_sph + off, s_rec + off,
-                                                  s_cb + s_run_coff[run], len, bs, bt, bpos, counters);
-                    if (key != ~0ull) {
-                        TriRec T;
-                        T.r0 = s_rec[off + bpos][0];
-                        T.r1 = s_rec[off + bpos][1];
-                        T.r2 = s_rec[off + bpos][2];
-                        T.r3 = s_rec[off + bpos][3];
-                        write_record_tri(m, rec, i, key, bs, bt, T);
-                    }
-                } else if (inside) {
-                    key = scan_list<COUNT>(m, q, site, bs, bt, counters);
-                    if (key != ~0ull) write_record(m, rec, i, key, bs, bt);
+            {
+                // long lists go to the long-list pass: one append per warp keeps a warp's
+                // queries (mostly one site) together in the queue
+                const unsigned lm = __ballot_sync(0xffffffffu, is_long);
+                if (lm) {
+                    int wbase = 0;
+                    if (lane == __ffs(lm) - 1) wbase = atomicAdd(n_long, __popc(lm));
+                    wbase = __shfl_sync(0xffffffffu, wbase, __ffs(lm) - 1);
+                    if (is_long) longq[wbase + __popc(lm & ((1u << lane) - 1u))] = make_int2(i, site);
                 }
-                if (key == ~0ull) {
-                    rest[atomicAdd(n_rest, 1)] = i;
-                    if (COUNT) atomicAdd(counters + C_OUTSIDE, 1ull);
+            }
+            if (!valid || is_long) continue;
+            unsigned long long key = ~0ull;
+            float bs = 0.0f, bt = 0.0f;
+            const int off = run >= 0 ? s_run_off[run] : -1;
+            if (inside && off >= 0) {
+                int bpos = 0;
+                key = scan_list_staged<COUNT>(m, q, site, s_ent + off, s_sph + off, s_rec + off, s_cb + s_run_coff[run],
+                                              len, bs, bt, bpos, counters);
+                if (key != ~0ull) {
+                    TriRec T;
+                    T.r0 = s_rec[off + bpos][0];
+                    T.r1 = s_rec[off + bpos][1];
+                    T.r2 = s_rec[off + bpos][2];
+                    T.r3 = s_rec[off + bpos][3];
+                    write_record_tri(m, rec, i, key, bs, bt, T);
                 }
+            } else if (inside) {
+                key = scan_list<COUNT>(m, q, site, bs, bt, counters);
+                if (key != ~0ull) write_record(m, rec, i, key, bs, bt);
+            }
+            if (key == ~0ull) {
+                rest[atomicAdd(n_rest, 1)] = i;
+                if (COUNT) atomicAdd(counters + C_OUTSIDE, 1ull);
             }
         }
         __syncthreads();  // the staged data and run tables are reused by the next iteration
@@ -472,14 +537,12 @@ static int run_query_staged(p2m_index* h, MeshData& m, const float* d_pts, int64
     const MeshView v = m.view();
     const int S = v.n_sites;
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
-    size_t scan_tmp = 0, sel_tmp = 0;
+    size_t scan_tmp = 0;
     P2M_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, scan_tmp, (int*)nullptr, (int*)nullptr, S + 2, s));
-    P2M_CUDA_TRY(cub::DeviceSelect::Flagged(nullptr, sel_tmp, (int2*)nullptr, (unsigned char*)nullptr, (int2*)nullptr,
-                                            (int*)nullptr, (int)n, s));
     const size_t a4 = up(sizeof(int) * n), a8 = up(sizeof(int2) * n), a16 = up(sizeof(float4) * n);
-    const size_t tmp_bytes = up(std::max(scan_tmp, sel_tmp)), site_bytes = up(sizeof(int) * (S + 2));
-    // rest ids, long queue, counters | key, rank, qsite | cand | flag | tmp | qs | rec | site count, first
-    const size_t total = a4 + a8 + 256 + 3 * a4 + a8 + up(n) + tmp_bytes + a16 + 2 * a16 + 2 * site_bytes;
+    const size_t tmp_bytes = up(scan_tmp), site_bytes = up(sizeof(int) * (S + 2));
+    // rest ids, long queue, counters | key, rank | tmp | qs | rec | site count, first
+    const size_t total = a4 + a8 + 256 + 2 * a4 + tmp_bytes + a16 + 2 * a16 + 2 * site_bytes;
     P2M_TRY(rest.ensure(total));
     char* p = rest.as<char>();
     int32_t* d_rest = reinterpret_cast<int32_t*>(p); p += a4;
@@ -487,9 +550,6 @@ static int run_query_staged(p2m_index* h, MeshData& m, const float* d_pts, int64
     int* d_cnt = reinterpret_cast<int*>(p); p += 256;  // [0] rest, [1] long, [2] head
     int* key = reinterpret_cast<int*>(p); p += a4;
     int* rank = reinterpret_cast<int*>(p); p += a4;
-    int* qsite = reinterpret_cast<int*>(p); p += a4;
-    int2* cand = reinterpret_cast<int2*>(p); p += a8;
-    unsigned char* flag = reinterpret_cast<unsigned char*>(p); p += up(n);
     void* tmp = p; p += tmp_bytes;
     float4* qs = reinterpret_cast<float4*>(p); p += a16;
     float4* rec = reinterpret_cast<float4*>(p); p += 2 * a16;
@@ -505,18 +565,17 @@ static int run_query_staged(p2m_index* h, MeshData& m, const float* d_pts, int64
         k_site_rank<false><<<blocks, threads, 0, s>>>(v, d_pts, n, key, rank, site_count, nullptr);
     P2M_CUDA_TRY(cudaGetLastError());
     P2M_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, scan_tmp, site_count, site_first, S + 2, s));
-    k_site_scatter<<<blocks, threads, 0, s>>>(d_pts, n, key, rank, site_first, qs, qsite);
+    k_site_scatter<<<blocks, threads, 0, s>>>(d_pts, n, key, rank, site_first, qs);
     P2M_CUDA_TRY(cudaGetLastError());
-    const int sblocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + kStageThreads - 1) / kStageThreads,
-                                                                    (int64_t)sm_count() * 32));
+    const int sblocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + kStageTile - 1) / kStageTile,
+                                                                    (int64_t)sm_count() * 16));
     if (counters)
-        k_query_staged<true><<<sblocks, kStageThreads, 0, s>>>(v, qs, qsite, n, d_rest, d_cnt, cand, flag, rec, counters);
+        k_query_staged<true><<<sblocks, kStageThreads, 0, s>>>(v, qs, site_first, n, d_rest, d_cnt, d_long, d_cnt + 1,
+                                                               rec, counters);
     else
-        k_query_staged<false><<<sblocks, kStageThreads, 0, s>>>(v, qs, qsite, n, d_rest, d_cnt, cand, flag, rec, nullptr);
+        k_query_staged<false><<<sblocks, kStageThreads, 0, s>>>(v, qs, site_first, n, d_rest, d_cnt, d_long, d_cnt + 1,
+                                                                rec, nullptr);
     P2M_CUDA_TRY(cudaGetLastError());
-    // long-list queries, in site order (each block of the warp pass then works through one
-    // site's queries)
-    P2M_CUDA_TRY(cub::DeviceSelect::Flagged(tmp, sel_tmp, cand, flag, d_long, d_cnt + 1, (int)n, s));
     const int wblocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, (int64_t)sm_count() * 16));
     if (counters)
         k_query_warp<true><<<wblocks, threads, 0, s>>>(v, d_pts, d_long, d_cnt + 1, d_dist, d_closest, d_tri, d_bary,
@@ -534,13 +593,15 @@ int run_query(p2m_index* h, MeshData& m, const float* d_pts, int64_t n, float* d
               int32_t* d_tri, float* d_bary, unsigned long long* counters, DevBuf& rest, cudaStream_t s) {
     const MeshView v = m.view();
     if (v.G == 0) return launch_bvh_closest(v, d_pts, nullptr, nullptr, n, d_dist, d_closest, d_tri, d_bary, index_status(h), s);
-    if (m.site_staged && n >= 4096)
+    // the site-staged schedule pays when sites have many queries each; a smaller call takes
+    // the Morton-ordered thread-per-query path instead
+    if (m.site_staged && n >= 4096 && n >= 16 * (int64_t)v.n_sites)
         return run_query_staged(h, m, d_pts, n, d_dist, d_closest, d_tri, d_bary, counters, rest, s);
     // scratch: rest ids [n], long queue [n] of int2, counters; for the sorted schedules also
     // the sort keys / permutation double buffers [4][n], per-query (query, site) pairs and long
     // flags, the temporary storage of the radix sorts and of the compaction, the points in
     // sorted order [n] float4 and the result records [n][2] float4
-    const bool sorted = m.sorted && n >= 4096 && n <= 0x7fffffff;
+    const bool sorted = (m.sorted || m.site_staged) && n >= 4096 && n <= 0x7fffffff;
     const bool by_site = sorted && m.site_sorted;
     int site_bits = 1;
     while ((1u << site_bits) <= (unsigned)v.n_sites) ++site_bits;  // keys 0..n_sites

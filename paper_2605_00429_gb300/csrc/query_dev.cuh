@@ -7,7 +7,7 @@
 
 namespace p2m {
 
-enum { C_OUTSIDE = 0, C_SITES = 1, C_TIES = 2, C_ROWS = 3, C_EXACT = 4 };
+enum { C_OUTSIDE = 0, C_SITES = 1, C_TIES = 2, C_ROWS = 3, C_EXACT = 4, C_LONG = 5, C_LONG_ROWS = 6 };
 
 __device__ __forceinline__ bool grid_cell(const MeshView& m, float3 q, int& cell) {
     const float fx = (q.x - m.lo.x) * m.inv_h.x;
@@ -20,15 +20,26 @@ __device__ __forceinline__ bool grid_cell(const MeshView& m, float3 q, int& cell
     return true;
 }
 
-// Nearest site among the grid cell's candidates.
-template <bool COUNT>
+// Nearest site among the grid cell's candidates.  IDS: read the candidates as site ids and
+// their positions from the site table (4 B per candidate, a small table that stays in cache);
+// else read the inline (x, y, z, id) candidates (one 16 B load each).
+template <bool COUNT, bool IDS = false>
 __device__ __forceinline__ int nearest_site(const MeshView& m, float3 q, int cell, unsigned long long* counters) {
     const int j0 = __ldg(m.cell_off + cell), j1 = __ldg(m.cell_off + cell + 1);
+    auto cand = [&](int j, int& s) {
+        if (IDS) {
+            s = __ldg(m.cell_id + j);
+            return __ldg(m.sites + s);
+        }
+        const float4 p = __ldg(m.cell_site + j);
+        s = __float_as_int(p.w);
+        return p;
+    };
     float bd = INFINITY, sd = INFINITY;
     int bs = -1;
     for (int j = j0; j < j1; ++j) {
-        const float4 p = __ldg(m.cell_site + j);
-        const int s = __float_as_int(p.w);
+        int s;
+        const float4 p = cand(j, s);
         const float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
         const float d2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
         if (d2 < bd || (d2 == bd && s < bs)) {
@@ -47,8 +58,8 @@ __device__ __forceinline__ int nearest_site(const MeshView& m, float3 q, int cel
         double best = 1e300;
         int bi = -1;
         for (int j = j0; j < j1; ++j) {
-            const float4 p = __ldg(m.cell_site + j);
-            const int s = __float_as_int(p.w);
+            int s;
+            const float4 p = cand(j, s);
             const float dx = q.x - p.x, dy = q.y - p.y, dz = q.z - p.z;
             if (fmaf(dx, dx, fmaf(dy, dy, dz * dz)) > lim) continue;
             const double ex = (double)q.x - (double)p.x, ey = (double)q.y - (double)p.y, ez = (double)q.z - (double)p.z;
@@ -338,6 +349,8 @@ __device__ __forceinline__ bool warp_scan_list(const MeshView& m, float3 q, int 
     if (COUNT) {
         atomicAdd(counters + C_ROWS, (unsigned long long)n_entries);
         atomicAdd(counters + C_EXACT, (unsigned long long)n_exact);
+        atomicAdd(counters + C_LONG_ROWS, (unsigned long long)n_entries);
+        if (lane == 0) atomicAdd(counters + C_LONG, 1ull);
     }
     return bhi != 0xffffffffu || blo != 0xffffffffu;
 }

@@ -169,9 +169,27 @@ def test_counters(p2m):
 
 @pytest.mark.parametrize("schedule", [1, 2, 3, 4, 5])
 def test_schedules_agree(p2m, schedule):
-    """Thread-per-query, warp-per-query and the mixed schedule give the same answers."""
+    """Thread-per-query, warp-per-query, the mixed and the site-staged schedules give the same
+    answers."""
     mesh, q = W.workload_large(50_000, k=4)
     base = _query(p2m.P2MIndex(mesh.verts, mesh.tris, schedule=0), q)
     other = _query(p2m.P2MIndex(mesh.verts, mesh.tris, schedule=schedule), q)
     assert np.array_equal(base[0], other[0]) and np.array_equal(base[2], other[2])
     check_parity(mesh, q[:5000], tuple(a[:5000] for a in other))
+
+
+@pytest.mark.parametrize("schedule", [2, 5])
+def test_schedules_agree_long_lists(p2m, schedule):
+    """On a rotationally symmetric mesh, where the auxiliary sites have lists longer than
+    long_list: the long-list passes give the same answers as schedule 0, and match the
+    oracle."""
+    mesh, q = W.workload_symmetric(60_000, n_ang=128, n_ax=32)
+    idx0 = p2m.P2MIndex(mesh.verts, mesh.tris, schedule=0)
+    base = _query(idx0, q)
+    idx = p2m.P2MIndex(mesh.verts, mesh.tris, schedule=schedule)
+    import torch
+    c = idx.counters(torch.from_numpy(q).cuda())
+    assert c["long_queries"] > 100, "this workload should exercise the long-list pass"
+    other = _query(idx, q)
+    assert np.array_equal(base[0], other[0]) and np.array_equal(base[2], other[2])
+    check_parity(mesh, q[:6000], tuple(a[:6000] for a in other))
