@@ -291,19 +291,24 @@ def run_ablation(args):
     cases = [
         ("sphere: icosphere(5), 20,480 faces, no noise; 1M queries uniform in 1.2x bbox",
          lambda: (W.icosphere(5), None)),
+        ("UV sphere 32x16, 960 faces; 1M queries uniform in 1.2x bbox", lambda: (W.uv_sphere(32, 16), None)),
         ("noisy sphere: icosphere(6) + noise, 81,920 faces; 1M queries as config 2",
          lambda: W.workload_large(1_000_000)),
-        ("cylinder + cone 256x64, 51,968 faces; 1M queries as config 3",
-         lambda: W.workload_symmetric(1_000_000, n_ang=256, n_ax=64)),
+        ("cylinder + cone 512x128, 203,776 faces; 1M queries as config 3",
+         lambda: W.workload_symmetric(1_000_000)),
     ]
+    # (label, build parameters): no augmentation, augmentation with the single Eq. 8 ball per
+    # auxiliary site, augmentation with its per-corner balls (the default)
+    modes = [("off", dict(enable_aux=0)), ("on, Eq. 8 ball", dict(enable_aux=1, aux_balls=0)),
+             ("on, corner balls", dict(enable_aux=1, aux_balls=1))]
     for desc, make in cases:
         mesh, q = make()
         if q is None:
             q = W.queries_uniform_box(mesh, 1_000_000, 1.2, seed=1)
         pts = torch.from_numpy(q).cuda()
-        for aux in (0, 1):
+        for label, prm in modes:
             t0 = time.perf_counter()
-            idx = p2m.P2MIndex(mesh.verts, mesh.tris, enable_aux=aux)
+            idx = p2m.P2MIndex(mesh.verts, mesh.tris, **prm)
             build_ms = (time.perf_counter() - t0) * 1e3
             st = idx.stats()
             c = idx.counters(pts)
@@ -316,11 +321,11 @@ def run_ablation(args):
             e1.record()
             torch.cuda.synchronize()
             ms = e0.elapsed_time(e1) / 5
-            print(json.dumps({"ablation": desc, "aux": aux, "build_ms": build_ms, "query_ms": ms,
+            print(json.dumps({"ablation": desc, "aux": label, "build_ms": build_ms, "query_ms": ms,
                               "queries_per_s": len(q) / (ms / 1e3), "max_list": st["max_row"],
                               "avg_list": st["avg_row"], "queried_entries": c["row_entries"] / len(q),
-                              "queried_exact": c["exact_tests"] / len(q), "sites": st["n_sites"],
-                              "aux_sites": st["n_aux_sites"], "nnz": st["nnz"]}), flush=True)
+                              "queried_exact": c["exact_tests"] / len(q), "long_queries": c["long_queries"],
+                              "sites": st["n_sites"], "aux_sites": st["n_aux_sites"], "nnz": st["nnz"]}), flush=True)
             del idx
 
 
@@ -397,6 +402,10 @@ def main():
 
     starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
     ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    # the library records CUDA events on the query's stream around its list-scan kernel (the
+    # dominant kernel); they are read after each step, outside the step's own events
+    idx.set_timing(True)
+    scan_ms = []
     sampler = ClockSampler(torch.cuda.current_device())
     sampler.start()
     barrier()
@@ -406,11 +415,14 @@ def main():
         starts[k].record(stream)
         idx.query(pts, out=out)
         ends[k].record(stream)
+        scan_ms.append(idx.query_timing()[0])
     torch.cuda.synchronize()
     barrier()
     clocks = sampler.stop()
+    idx.set_timing(False)
     step_ms = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     ms = reduce_max_ms(float(np.mean(step_ms)), world, dev)
+    kernel_ms = float(np.mean(scan_ms))
     value = replicas_value(n, ms, world)
 
     pk, pk_kind = peaks()
@@ -419,7 +431,11 @@ def main():
     alu_peak = sm_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12  # TFLOP/s
     flops = (FLOP_PER_SITE * cnt["site_candidates"] + FLOP_PER_ROW_ENTRY * cnt["row_entries"] +
              FLOP_PER_EXACT * cnt["exact_tests"] + FLOP_PER_QUERY * n)
-    achieved = flops / (ms / 1e3) / 1e12
+    # the list-scan kernel's own work: the short lists' entries and exact tests (the long lists'
+    # belong to the warp pass) and its per-query bound setup and record
+    scan_flops = (FLOP_PER_ROW_ENTRY * (cnt["row_entries"] - cnt["long_entries"]) +
+                  FLOP_PER_EXACT * cnt["exact_tests"] + FLOP_PER_QUERY * n)
+    achieved = scan_flops / (kernel_ms / 1e3) / 1e12 if kernel_ms > 0 else flops / (ms / 1e3) / 1e12
     hbm_gbs = BYTES_PER_QUERY * n / (ms / 1e3) / 1e9
 
     line = {"metric": metric_name(args.config), "value": value, "unit": "queries/s", "n_gpus": world, "steps": args.steps,
@@ -431,7 +447,10 @@ def main():
             "roofline": {"bound": "alu", "achieved": achieved, "peak": alu_peak, "unit": "TFLOP/s",
                          "frac": achieved / alu_peak, "traffic": profiled_traffic(args.config, n),
                          "l1tex_pct_ncu": profiled_l1tex_pct(args.config),
-                         "kernel": "k_query_thread + k_query_warp (one query pass)",
+                         "kernel": "k_query_staged" if args.schedule == 5 else "k_query_thread",
+                         "kernel_ms": kernel_ms,
+                         "kernel_share_of_step": kernel_ms / ms if ms > 0 else None,
+                         "step_flops_achieved": flops / (ms / 1e3) / 1e12,
                          "peak_kind": f"{sm_count} SMs x {FP32_LANES_PER_SM} FP32 FMA lanes x max SM clock "
                                       f"from {pk_kind} peaks",
                          "sm_count": sm_count,

@@ -84,7 +84,7 @@ typedef struct {
     /* Query schedule [5]: 5 = queries counting-sorted by nearest site, then each block stages
      * the short lists of the sites of its 1024 queries (entries, bounding spheres, triangle
      * records, chunk boxes) in shared memory and scans them thread per query; lists longer
-     * than long_list take a warp-cooperative best-first scan (a call with fewer than 16
+     * than long_list take a warp-cooperative best-first scan (a call with fewer than 48
      * queries per site takes schedule 0 instead); 0 = queries sorted by the Morton code of
      * their grid cell, then thread per query for lists up to long_list entries and the
      * warp-cooperative scan for longer lists; 1 = thread per query for every list; 2 = warp
@@ -296,6 +296,16 @@ int p2m_get_sites(const p2m_index* h, int mesh, float* h_sites, double* h_ref, i
 
 /* Interception lists (CSR) of mesh `mesh`: h_offsets[n_sites+1], h_tri_ids[nnz]. */
 int p2m_get_lists(const p2m_index* h, int mesh, int64_t* h_offsets, int32_t* h_tri_ids);
+
+/* Kernel timing of the query path (for benchmarks).  With on != 0, every later query call on
+ * the index records CUDA events on its stream: at the start, around its list-scan kernel
+ * (k_query_staged, or k_query_thread in the Morton-ordered schedules; the dominant kernel)
+ * and at the end.  p2m_query_timing then returns, for the last call, h_ms[0] = the list-scan
+ * kernel's milliseconds (0 when the call had none) and h_ms[1] = the whole launch sequence's;
+ * it waits for the call's end event.  Errors: INVALID_ARG (NULL, timing off, no timed call),
+ * CUDA. */
+int p2m_set_timing(p2m_index* h, int on);
+int p2m_query_timing(p2m_index* h, double* h_ms);
 
 /* Triangle BVH of mesh `mesh` (the LBVH of Section 3.3 "Implementation Details" that the
  * corner balls are tested against, and the exact search for points outside D uses).

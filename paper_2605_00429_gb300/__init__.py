@@ -85,6 +85,8 @@ SIGNATURES = {
     "p2m_get_lists": ([_P, _I, _P, _P], _I),
     "p2m_get_balls": ([_P, _I, _P, _P, _P], _I),
     "p2m_get_bvh": ([_P, _I, _P, _P, _P, _P], _I),
+    "p2m_set_timing": ([_P, _I], _I),
+    "p2m_query_timing": ([_P, _P], _I),
     "p2m_voronoi_cells": ([_P, _I64, _P, _P, _I, _P, _P, _P, _P], _I),
     "p2m_voronoi_cells_device": ([_P, _I64, _P, _P, _I, _P, _P, _P, _P, _P, _P], _I),
     "p2m_query_noalloc": ([_P, _P, _I64, _P, _P, _P, _P, _P], _I),
@@ -318,6 +320,16 @@ class P2MIndex:
                                      _dptr(tri), _dptr(bary), int(mode), int(bool(use_graph)),
                                      _stream_ptr(stream)))
         return out
+
+    def set_timing(self, on=True):
+        """Record CUDA events around the list-scan kernel of every later query call."""
+        _check(lib().p2m_set_timing(self._h, int(bool(on))))
+
+    def query_timing(self):
+        """(list-scan kernel ms, whole call ms) of the last timed query call."""
+        out = np.zeros(2)
+        _check(lib().p2m_query_timing(self._h, out.ctypes.data_as(_P)))
+        return float(out[0]), float(out[1])
 
     # ---------------------------------------------------------------- introspection
     def stats(self) -> dict:

@@ -102,13 +102,13 @@ MeshView MeshData::view() const {
     v.l1box = d_l1box.as<const float4>();
     v.long_row = long_row;
     v.cell_off = d_cell_off.as<const int32_t>();
-    v.cell_site = d_cell_site.as<const float4>();
     v.cell_id = d_cell_id.as<const int32_t>();
     v.G = G;
     v.lo = g_lo;
     v.hi = g_hi;
     v.inv_h = g_inv_h;
     v.prune_abs = (float)(diag * std::ldexp(1.0, -22));
+    v.spacing = spacing;
     v.n_tris = (int)n_tris;
     v.n_sites = (int)(site_pos.size() / 3);
     return v;
@@ -154,11 +154,19 @@ int check_call(const p2m_index* h, int64_t n, const char* what) {
     return P2M_OK;
 }
 
+void timing_mark(p2m_index* h, int k, cudaStream_t s) {
+    if (!h->timing) return;
+    cudaEventRecord(h->tev[k], s);
+    if (k == 3) h->timed_call = true;
+}
+
 }  // namespace p2m
 
 p2m_index::~p2m_index() {
     for (auto& st : streams)
         if (st) cudaStreamDestroy(st);
+    for (auto& e : tev)
+        if (e) cudaEventDestroy(e);
 }
 
 // ----------------------------------------------------------------------------- validation
@@ -526,6 +534,28 @@ int p2m_get_lists(const p2m_index* h, int mesh, int64_t* h_offsets, int32_t* h_t
         P2M_CUDA_TRY(cudaMemcpy(ent.data(), m->d_row_ent.p, sizeof(int2) * m->nnz, cudaMemcpyDeviceToHost));
         for (int64_t k = 0; k < m->nnz; ++k) h_tri_ids[k] = m->orig[ent[k].x];  // caller's triangle ids
     }
+    return P2M_OK;
+}
+
+int p2m_set_timing(p2m_index* h, int on) {
+    if (!h) return fail(P2M_ERR_INVALID_ARG, "NULL index");
+    if (on)
+        for (auto& e : h->tev)
+            if (!e) P2M_CUDA_TRY(cudaEventCreate(&e));
+    h->timing = on != 0;
+    h->timed_call = false;
+    return P2M_OK;
+}
+
+int p2m_query_timing(p2m_index* h, double* h_ms) {
+    if (!h || !h_ms) return fail(P2M_ERR_INVALID_ARG, "NULL index or output");
+    if (!h->timing || !h->timed_call) return fail(P2M_ERR_INVALID_ARG, "timing is off, or no query call was timed");
+    P2M_CUDA_TRY(cudaEventSynchronize(h->tev[3]));
+    float a = 0.f, b = 0.f;
+    P2M_CUDA_TRY(cudaEventElapsedTime(&a, h->tev[1], h->tev[2]));
+    P2M_CUDA_TRY(cudaEventElapsedTime(&b, h->tev[0], h->tev[3]));
+    h_ms[0] = a;
+    h_ms[1] = b;
     return P2M_OK;
 }
 

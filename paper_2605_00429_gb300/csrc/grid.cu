@@ -17,7 +17,8 @@
 //
 // Count pass (cells' candidate counts, atomics), scan, fill pass (atomic slots), then each
 // cell's list is sorted by site id (the order does not change any result; it makes the grid
-// deterministic) and packed as (x, y, z, id) so a query reads one contiguous run.
+// deterministic).  A query reads its cell's run of ids and the sites' positions from the site
+// table.
 #include <algorithm>
 #include <atomic>
 #include <cmath>
@@ -167,16 +168,6 @@ __global__ void __launch_bounds__(32 * kRasterWarps)
             if (!FILL) item_count[it] = emitted;
             else if (emitted != item_count[it]) atomicOr(status, ST_BAD);  // both passes walk alike
         }
-    }
-}
-
-// Candidate entries (site xyz, site id in w) from the sorted site ids.
-__global__ void k_grid_pack(const int* __restrict__ ids, int64_t n, const float4* __restrict__ sites,
-                            float4* __restrict__ out) {
-    for (int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; j < n; j += (int64_t)gridDim.x * blockDim.x) {
-        const int s = ids[j];
-        const float4 p = __ldg(sites + s);
-        out[j] = make_float4(p.x, p.y, p.z, __int_as_float(s));
     }
 }
 
@@ -331,12 +322,6 @@ int build_grid(MeshData& m, const SiteSet& ss, int G, unsigned* status, cudaStre
     if (total > 0)
         P2M_CUDA_TRY(cub::DeviceSegmentedSort::SortKeys(tmp.p, tb2, d_ids.as<int>(), d_ids2.as<int>(), (int)total,
                                                         (int)n_cells, d_off.as<int>(), d_off.as<int>() + 1, s));
-    P2M_TRY(m.d_cell_site.alloc(sizeof(float4) * std::max<int64_t>(total, 1)));
-    if (total > 0) {
-        k_grid_pack<<<(int)std::min<int64_t>((total + 255) / 256, (int64_t)sm_count() * 32), 256, 0, s>>>(
-            d_ids2.as<int>(), total, sites, m.d_cell_site.as<float4>());
-        P2M_CUDA_TRY(cudaGetLastError());
-    }
     m.d_cell_off = std::move(d_off);
     m.d_cell_id = std::move(d_ids2);
     P2M_CUDA_TRY(cudaStreamSynchronize(s));

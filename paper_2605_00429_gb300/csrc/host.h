@@ -55,6 +55,11 @@ struct p2m_index {
     p2m::DevBuf pipe[kPipe][5];    // pts, dist, closest, tri, bary
     p2m::DevBuf pipe_rest[kPipe];
     p2m::DevBuf grad_acc;      // fixed-point vertex-gradient accumulator
+    // kernel timing (p2m_set_timing): events at the call's start, around its list-scan
+    // kernel, and at its end
+    bool timing = false;
+    bool timed_call = false;
+    cudaEvent_t tev[4] = {nullptr, nullptr, nullptr, nullptr};
     p2m::DevBuf sign_scratch;  // triangle ids / barycentrics for the signed query
     ~p2m_index();
 };
@@ -68,6 +73,8 @@ int check_status_word(p2m_index* h, cudaStream_t s, const char* what);
 // built on must be current (its buffers live there), and a call takes at most 2^31 - 1
 // points (query positions are int32 inside the kernels).
 int check_call(const p2m_index* h, int64_t n, const char* what);
+// With timing on, records event k (0 start, 1 before the list scan, 2 after it, 3 end) on s.
+void timing_mark(p2m_index* h, int k, cudaStream_t s);
 
 // Sites, Delaunay, augmentation, corner balls, interception lists, nearest-site grid.
 int build_partition(MeshData& m, const p2m_build_params& prm, p2m_index* h, cudaStream_t s);

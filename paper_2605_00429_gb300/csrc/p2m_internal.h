@@ -104,13 +104,13 @@ struct MeshView {
     const int32_t* l1_off;  // [S+1] first level-1 box (32 chunks = 1024 entries) of each list
     const float4* l1box;    // [n_l1][2]
     const int32_t* cell_off;// [G^3+1] nearest-site grid CSR
-    const float4* cell_site;// candidates: (x, y, z, site id as int bits)
-    const int32_t* cell_id; // the same candidates as site ids (4 B each; positions from `sites`)
+    const int32_t* cell_id; // candidate site ids (positions from `sites`)
     int G;                  // grid cells per axis (0 => no grid: every query takes the BVH path)
     float3 lo;              // domain D lower corner
     float3 inv_h;           // 1 / grid cell size
     float3 hi;              // domain D upper corner
     float prune_abs;        // absolute prune slack
+    float spacing;          // mean spacing of the vertex sites (sqrt(area / sites))
     int n_tris;
     int n_sites;
     int long_row;           // lists longer than this go to the warp-per-query scan
@@ -135,13 +135,14 @@ struct MeshData {
     DevBuf d_snorm, d_vnorm;     // pseudonormals for the sign: [T][4] (face, edges 01/12/20), [V]
     std::vector<int32_t> orig;   // host copy of d_orig
     Bvh bvh;
-    DevBuf d_sites, d_refs, d_row_off, d_row_tri, d_row_key, d_row_ent, d_cell_off, d_cell_site, d_cell_id, d_chunk_off, d_cbox, d_l1_off, d_l1box;
+    DevBuf d_sites, d_refs, d_row_off, d_row_tri, d_row_key, d_row_ent, d_cell_off, d_cell_id, d_chunk_off, d_cbox, d_l1_off, d_l1box;
     int64_t nnz = 0, n_chunks = 0;
     int long_row = 256;
     bool sorted = true;          // process queries in grid-cell Morton order
     bool site_sorted = false;    // then regroup them by nearest site before the list scan
     bool site_staged = false;    // queries counting-sorted by nearest site, lists staged in shared memory
     int G = 0;
+    float spacing = 0.0f;
     float3 g_lo{}, g_hi{}, g_inv_h{};
     p2m_stats stats{};
     MeshView view() const;

@@ -524,13 +524,14 @@ int build_partition(MeshData& m, const p2m_build_params& prm, p2m_index* h, cuda
             const double n[3] = {e0[1] * e1[2] - e0[2] * e1[1], e0[2] * e1[0] - e0[0] * e1[2], e0[0] * e1[1] - e0[1] * e1[0]};
             area += 0.5 * std::sqrt(n[0] * n[0] + n[1] * n[1] + n[2] * n[2]);
         }
+        const double spacing = std::sqrt(std::max(area, 1e-300) / std::max(1, n_vsites));
+        m.spacing = (float)spacing;
         int G = prm.nn_grid_res;
         if (G <= 0) {
-            const double spacing = std::sqrt(std::max(area, 1e-300) / std::max(1, n_vsites));
             double ext = 0;
             for (int k = 0; k < 3; ++k) ext = std::max(ext, m.dom_hi[k] - m.dom_lo[k]);
-            G = (int)std::lround(ext / (1.1 * spacing));
-            G = std::max(8, std::min(G, 192));
+            G = (int)std::lround(ext / (0.8 * spacing));
+            G = std::max(8, std::min(G, 256));
         }
         P2M_TRY(build_grid(m, ss, G, status, s));
         P2M_TRY(check_status_word(h, s, "nearest-site grid"));

@@ -78,15 +78,18 @@ __global__ void __launch_bounds__(256, 6) k_query_thread(MeshView m, const float
 // read the same staged entry at the same time (a broadcast), where the thread-per-query
 // kernels gather the same data through L1 once per lane.
 
-constexpr int kStage = 448;        // list entries one block stages
-constexpr int kStageChunks = 32;   // chunk boxes one block stages
+constexpr int kStage = 384;        // list entries one block stages
 constexpr int kStageThreads = 256;
-constexpr int kStagePer = 4;       // queries per thread in one block iteration
-constexpr int kStageTile = kStageThreads * kStagePer;
+constexpr int kStagePer = 4;       // queries per thread in one block iteration (at most)
+constexpr int kDqBuckets = 8;      // distance classes of the queries of one site (see k_site_rank)
 constexpr int kStageRuns = 64;     // runs (sites) one tile may span; the rest scan unstaged
 
 // Pass 1, queries in input order: nearest site (K2) and the query's rank among the queries
-// of that site.  A point outside D gets the key n_sites.
+// of the same key.  The key is site * kDqBuckets + a distance class of the query from the site
+// (below 1, 2, 4, ..., 64 site spacings, or beyond): the site's queries then come in order of
+// distance,
+// so that the lanes of a warp, which scan the same list, have similar bounds and stop at
+// similar entries.  A point outside D gets the key n_sites * kDqBuckets.
 template <bool COUNT>
 __global__ void __launch_bounds__(256) k_site_rank(MeshView m, const float* __restrict__ pts, int64_t n,
                                                   int* __restrict__ key, int* __restrict__ rank,
@@ -95,8 +98,16 @@ __global__ void __launch_bounds__(256) k_site_rank(MeshView m, const float* __re
         const float3 q = make_float3(pts[3 * i], pts[3 * i + 1], pts[3 * i + 2]);
         int cell;
         int site = -1;
-        if (grid_cell(m, q, cell)) site = nearest_site<COUNT, true>(m, q, cell, counters);
-        const int k = site >= 0 ? site : m.n_sites;
+        if (grid_cell(m, q, cell)) site = nearest_site<COUNT>(m, q, cell, counters);
+        int k = m.n_sites * kDqBuckets;
+        if (site >= 0) {
+            const float4 sp = __ldg(m.sites + site);
+            const float dx = q.x - sp.x, dy = q.y - sp.y, dz = q.z - sp.z;
+            const float d = sqrtf(fmaf(dx, dx, fmaf(dy, dy, dz * dz)));
+            int b = 0;
+            for (float t = m.spacing; b < kDqBuckets - 1 && d >= t; t *= 2.0f) ++b;
+            k = site * kDqBuckets + b;
+        }
         key[i] = k;
         rank[i] = atomicAdd(count + k, 1);
     }
@@ -121,38 +132,41 @@ __device__ __forceinline__ void write_record_tri(const MeshView& m, float4* __re
     rec[2 * i + 1] = make_float4(__int_as_float(__ldg(m.orig + f)), 1.0f - s - t, s, t);
 }
 
-// Pass 3: the list scan over the site-ordered queries, kStageTile per block iteration.  The
-// tile's runs (sites) come from the site offsets `first` (first[s] = the first slot of site
-// s, first[n_sites + 1] = n; key n_sites = outside D): a binary search finds the site of the
-// tile's first query, and the next offsets give the runs.  Whole short lists of the runs are
-// staged while they fit; each thread then scans kStagePer queries (lanes of a warp take
+// Pass 3: the list scan over the site-ordered queries, per * 256 per block iteration.  The
+// tile's runs (sites) come from the key offsets `first` (first[s * kDqBuckets] = the first
+// slot of site s, first[n_sites * kDqBuckets + 1] = n; site n_sites = outside D): a binary
+// search finds the site of the
+// tile's first query, and the next offsets give the runs.  Whole short lists of the runs
+// (entries, bounding spheres, triangle records) are staged while they fit; each thread then
+// scans per (1..kStagePer, fewer for small calls so that every SM gets tiles) queries (lanes of a warp take
 // consecutive queries, mostly of one site, so their reads of the staged list are broadcasts).
 template <bool COUNT>
-__global__ void __launch_bounds__(kStageThreads, 4)
-    k_query_staged(MeshView m, const float4* __restrict__ qs, const int* __restrict__ first, int64_t n,
+__global__ void __launch_bounds__(kStageThreads, 5)
+    k_query_staged(MeshView m, const float4* __restrict__ qs, const int* __restrict__ first, int64_t n, int per,
                    int32_t* __restrict__ rest, int* __restrict__ n_rest, int2* __restrict__ longq,
                    int* __restrict__ n_long, float4* __restrict__ rec, unsigned long long* counters) {
     __shared__ int2 s_ent[kStage];
     __shared__ float4 s_sph[kStage];
     __shared__ float4 s_rec[kStage][4];
-    __shared__ float4 s_cb[kStageChunks][3];
-    // runs: site, first slot, list start / length, chunk start / count, staged entry and
-    // chunk offsets (-1: not staged)
+    // runs: site, first slot, list start and length, staged entry offset (-1: not staged)
     __shared__ int s_run_site[kStageRuns], s_run_beg[kStageRuns + 1];
-    __shared__ int s_run_row[kStageRuns], s_run_len[kStageRuns], s_run_gch[kStageRuns], s_run_nch[kStageRuns];
-    __shared__ int s_run_off[kStageRuns], s_run_coff[kStageRuns];
-    __shared__ int s_st_run[kStageRuns], s_st_off[kStageRuns + 1], s_st_coff[kStageRuns + 1];
+    __shared__ int s_run_row[kStageRuns], s_run_len[kStageRuns];
+    __shared__ int s_run_off[kStageRuns];
+    __shared__ int s_st_run[kStageRuns], s_st_off[kStageRuns + 1];
     __shared__ int s_nruns, s_nstaged, s_site0;
     const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
     const int S = m.n_sites;
-    for (int64_t base = (int64_t)blockIdx.x * kStageTile; base < n; base += (int64_t)gridDim.x * kStageTile) {
-        const int64_t tend = min(base + (int64_t)kStageTile, n);
+    // first slot of site s's queries (all its distance classes); S: the points outside D
+    auto site_first = [&](int s) { return s <= S ? __ldg(first + (int64_t)s * kDqBuckets) : (int)n; };
+    const int tile = kStageThreads * per;
+    for (int64_t base = (int64_t)blockIdx.x * tile; base < n; base += (int64_t)gridDim.x * tile) {
+        const int64_t tend = min(base + (int64_t)tile, n);
         if (tid == 0) {
             // the site of the tile's first query: the last s in [0, S] with first[s] <= base
             int lo = 0, hi = S;
             while (lo < hi) {
                 const int mid = (lo + hi + 1) >> 1;
-                if (__ldg(first + mid) <= base) lo = mid;
+                if (site_first(mid) <= base) lo = mid;
                 else hi = mid - 1;
             }
             s_site0 = lo;
@@ -163,8 +177,8 @@ __global__ void __launch_bounds__(kStageThreads, 4)
             int nr = 0, s = s_site0;
             while (nr < kStageRuns && s <= S) {
                 const int ss = s + lane;
-                const int f0 = ss <= S ? __ldg(first + ss) : (int)n;
-                const int f1 = ss <= S ? __ldg(first + ss + 1) : (int)n;
+                const int f0 = site_first(ss);
+                const int f1 = site_first(ss + 1);
                 const bool has = ss <= S && f1 > f0 && f0 < tend && f1 > base;
                 const unsigned hm = __ballot_sync(0xffffffffu, has);
                 const int r = nr + __popc(hm & ((1u << lane) - 1u));
@@ -183,46 +197,38 @@ __global__ void __launch_bounds__(kStageThreads, 4)
         const int nr = s_nruns;
         if (tid < nr) {
             const int st = s_run_site[tid];
-            int r0 = 0, len = 0, g0 = 0, nch = 0;
+            int r0 = 0, len = 0;
             if (st < S) {
                 r0 = __ldg(m.row_off + st);
                 len = __ldg(m.row_off + st + 1) - r0;
-                g0 = __ldg(m.chunk_off + st);
-                nch = __ldg(m.chunk_off + st + 1) - g0;
             }
             s_run_row[tid] = r0;
             s_run_len[tid] = len;
-            s_run_gch[tid] = g0;
-            s_run_nch[tid] = nch;
         }
         __syncthreads();
         if (tid == 0) {
             // stage whole short lists in run order while they fit
-            int cum = 0, ch = 0, k = 0;
+            int cum = 0, k = 0;
             for (int r = 0; r < nr; ++r) {
-                const int len = s_run_len[r], nch = s_run_nch[r];
-                if (s_run_site[r] < S && len > 0 && len <= m.long_row && cum + len <= kStage && ch + nch <= kStageChunks) {
+                const int len = s_run_len[r];
+                if (s_run_site[r] < S && len > 0 && len <= m.long_row && cum + len <= kStage) {
                     s_run_off[r] = cum;
-                    s_run_coff[r] = ch;
                     s_st_run[k] = r;
                     s_st_off[k] = cum;
-                    s_st_coff[k] = ch;
                     cum += len;
-                    ch += nch;
                     ++k;
                 } else {
                     s_run_off[r] = -1;
                 }
             }
             s_st_off[k] = cum;
-            s_st_coff[k] = ch;
             s_nstaged = k;
             // queries past the last run (a tile spanning more than kStageRuns sites) scan
             // unstaged; mark where the runs end
             s_run_beg[nr] = nr < kStageRuns ? (int)tend : s_run_beg[nr - 1];
         }
         __syncthreads();
-        const int nst = s_nstaged, n_ent = s_st_off[nst], n_ch = s_st_coff[nst];
+        const int nst = s_nstaged, n_ent = s_st_off[nst];
         for (int e = tid; e < n_ent; e += kStageThreads) {
             int lo = 0, hi = nst - 1;
             while (lo < hi) {
@@ -239,20 +245,8 @@ __global__ void __launch_bounds__(kStageThreads, 4)
             s_rec[e][2] = __ldg(tp + 2);
             s_rec[e][3] = __ldg(tp + 3);
         }
-        for (int c = tid; c < n_ch; c += kStageThreads) {
-            int lo = 0, hi = nst - 1;
-            while (lo < hi) {
-                const int mid = (lo + hi + 1) >> 1;
-                if (s_st_coff[mid] <= c) lo = mid;
-                else hi = mid - 1;
-            }
-            const float4* r = m.cbox + 3 * ((int64_t)s_run_gch[s_st_run[lo]] + (c - s_st_coff[lo]));
-            s_cb[c][0] = __ldg(r);
-            s_cb[c][1] = __ldg(r + 1);
-            s_cb[c][2] = __ldg(r + 2);
-        }
         __syncthreads();
-        for (int k = 0; k < kStagePer; ++k) {
+        for (int k = 0; k < per; ++k) {
             if (base + k * kStageThreads >= tend) break;  // uniform over the block
             const int64_t j = base + k * kStageThreads + tid;
             const bool valid = j < tend;
@@ -278,7 +272,7 @@ __global__ void __launch_bounds__(kStageThreads, 4)
                     int lo = 0, hi = S;
                     while (lo < hi) {
                         const int mid = (lo + hi + 1) >> 1;
-                        if (__ldg(first + mid) <= j) lo = mid;
+                        if (site_first(mid) <= j) lo = mid;
                         else hi = mid - 1;
                     }
                     site = lo;
@@ -306,8 +300,8 @@ __global__ void __launch_bounds__(kStageThreads, 4)
             const int off = run >= 0 ? s_run_off[run] : -1;
             if (inside && off >= 0) {
                 int bpos = 0;
-                key = scan_list_staged<COUNT>(m, q, site, s_ent + off, s_sph + off, s_rec + off, s_cb + s_run_coff[run],
-                                              len, bs, bt, bpos, counters);
+                key = scan_list_staged<COUNT>(m, q, site, s_ent + off, s_sph + off, s_rec + off, len, bs, bt, bpos,
+                                              counters);
                 if (key != ~0ull) {
                     TriRec T;
                     T.r0 = s_rec[off + bpos][0];
@@ -456,9 +450,12 @@ __global__ void __launch_bounds__(256) k_query_warp(MeshView m, const float* __r
     }
     __shared__ int s_base, s_next;
     const int lane = threadIdx.x & 31;
+    // runs of at most kSeg entries; shorter when the queue is short, so that it spreads over
+    // the SMs instead of leaving a few blocks with long serial runs
+    const int seg = max(8, min(kSeg, nq / (2 * (int)gridDim.x)));
     while (true) {
         if (threadIdx.x == 0) {
-            s_base = atomicAdd(head, kSeg);
+            s_base = atomicAdd(head, seg);
             s_next = 0;
         }
         __syncthreads();
@@ -468,7 +465,7 @@ __global__ void __launch_bounds__(256) k_query_warp(MeshView m, const float* __r
             int j = 0;
             if (lane == 0) j = atomicAdd(&s_next, 1);
             j = __shfl_sync(0xffffffffu, j, 0);
-            if (j >= kSeg || base + j >= nq) break;
+            if (j >= seg || base + j >= nq) break;
             warp_query_one<COUNT>(m, pts, longq[base + j], dist, closest, tri_out, bary, rest, n_rest, counters,
                                   rec);
         }
@@ -538,9 +535,10 @@ static int run_query_staged(p2m_index* h, MeshData& m, const float* d_pts, int64
     const int S = v.n_sites;
     auto up = [](size_t b) { return (b + 255) / 256 * 256; };
     size_t scan_tmp = 0;
-    P2M_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, scan_tmp, (int*)nullptr, (int*)nullptr, S + 2, s));
+    const int K = S * kDqBuckets + 2;  // keys 0 .. S * kDqBuckets, and the end
+    P2M_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, scan_tmp, (int*)nullptr, (int*)nullptr, K, s));
     const size_t a4 = up(sizeof(int) * n), a8 = up(sizeof(int2) * n), a16 = up(sizeof(float4) * n);
-    const size_t tmp_bytes = up(scan_tmp), site_bytes = up(sizeof(int) * (S + 2));
+    const size_t tmp_bytes = up(scan_tmp), site_bytes = up(sizeof(int) * K);
     // rest ids, long queue, counters | key, rank | tmp | qs | rec | site count, first
     const size_t total = a4 + a8 + 256 + 2 * a4 + tmp_bytes + a16 + 2 * a16 + 2 * site_bytes;
     P2M_TRY(rest.ensure(total));
@@ -556,7 +554,7 @@ static int run_query_staged(p2m_index* h, MeshData& m, const float* d_pts, int64
     int* site_count = reinterpret_cast<int*>(p); p += site_bytes;
     int* site_first = reinterpret_cast<int*>(p);
     P2M_CUDA_TRY(cudaMemsetAsync(d_cnt, 0, 4 * sizeof(int), s));
-    P2M_CUDA_TRY(cudaMemsetAsync(site_count, 0, sizeof(int) * (S + 2), s));
+    P2M_CUDA_TRY(cudaMemsetAsync(site_count, 0, sizeof(int) * K, s));
     const int threads = 256;
     const int blocks = query_grid_blocks(n, threads);
     if (counters)
@@ -564,18 +562,24 @@ static int run_query_staged(p2m_index* h, MeshData& m, const float* d_pts, int64
     else
         k_site_rank<false><<<blocks, threads, 0, s>>>(v, d_pts, n, key, rank, site_count, nullptr);
     P2M_CUDA_TRY(cudaGetLastError());
-    P2M_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, scan_tmp, site_count, site_first, S + 2, s));
+    P2M_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp, scan_tmp, site_count, site_first, K, s));
     k_site_scatter<<<blocks, threads, 0, s>>>(d_pts, n, key, rank, site_first, qs);
     P2M_CUDA_TRY(cudaGetLastError());
-    const int sblocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + kStageTile - 1) / kStageTile,
-                                                                    (int64_t)sm_count() * 16));
+    // queries per thread: up to kStagePer, fewer when the call would not give every resident
+    // block (5 per SM) a tile
+    const int64_t resident = (int64_t)sm_count() * 5;
+    const int per = (int)std::max<int64_t>(1, std::min<int64_t>(kStagePer, n / (resident * kStageThreads)));
+    const int sblocks = (int)std::max<int64_t>(
+        1, std::min<int64_t>((n + (int64_t)kStageThreads * per - 1) / ((int64_t)kStageThreads * per), resident * 4));
+    timing_mark(h, 1, s);
     if (counters)
-        k_query_staged<true><<<sblocks, kStageThreads, 0, s>>>(v, qs, site_first, n, d_rest, d_cnt, d_long, d_cnt + 1,
+        k_query_staged<true><<<sblocks, kStageThreads, 0, s>>>(v, qs, site_first, n, per, d_rest, d_cnt, d_long, d_cnt + 1,
                                                                rec, counters);
     else
-        k_query_staged<false><<<sblocks, kStageThreads, 0, s>>>(v, qs, site_first, n, d_rest, d_cnt, d_long, d_cnt + 1,
+        k_query_staged<false><<<sblocks, kStageThreads, 0, s>>>(v, qs, site_first, n, per, d_rest, d_cnt, d_long, d_cnt + 1,
                                                                 rec, nullptr);
     P2M_CUDA_TRY(cudaGetLastError());
+    timing_mark(h, 2, s);
     const int wblocks = (int)std::max<int64_t>(1, std::min<int64_t>((n + 7) / 8, (int64_t)sm_count() * 16));
     if (counters)
         k_query_warp<true><<<wblocks, threads, 0, s>>>(v, d_pts, d_long, d_cnt + 1, d_dist, d_closest, d_tri, d_bary,
@@ -589,13 +593,26 @@ static int run_query_staged(p2m_index* h, MeshData& m, const float* d_pts, int64
     return launch_bvh_closest(v, d_pts, d_rest, d_cnt, n, d_dist, d_closest, d_tri, d_bary, index_status(h), s);
 }
 
+static int run_query_impl(p2m_index* h, MeshData& m, const float* d_pts, int64_t n, float* d_dist, float* d_closest,
+                          int32_t* d_tri, float* d_bary, unsigned long long* counters, DevBuf& rest, cudaStream_t s);
+
 int run_query(p2m_index* h, MeshData& m, const float* d_pts, int64_t n, float* d_dist, float* d_closest,
               int32_t* d_tri, float* d_bary, unsigned long long* counters, DevBuf& rest, cudaStream_t s) {
+    timing_mark(h, 0, s);
+    timing_mark(h, 1, s);  // moved to the list scan by the schedules that have one
+    timing_mark(h, 2, s);
+    const int rc = run_query_impl(h, m, d_pts, n, d_dist, d_closest, d_tri, d_bary, counters, rest, s);
+    timing_mark(h, 3, s);
+    return rc;
+}
+
+static int run_query_impl(p2m_index* h, MeshData& m, const float* d_pts, int64_t n, float* d_dist, float* d_closest,
+                          int32_t* d_tri, float* d_bary, unsigned long long* counters, DevBuf& rest, cudaStream_t s) {
     const MeshView v = m.view();
     if (v.G == 0) return launch_bvh_closest(v, d_pts, nullptr, nullptr, n, d_dist, d_closest, d_tri, d_bary, index_status(h), s);
     // the site-staged schedule pays when sites have many queries each; a smaller call takes
     // the Morton-ordered thread-per-query path instead
-    if (m.site_staged && n >= 4096 && n >= 16 * (int64_t)v.n_sites)
+    if (m.site_staged && n >= 4096 && n >= 48 * (int64_t)v.n_sites)
         return run_query_staged(h, m, d_pts, n, d_dist, d_closest, d_tri, d_bary, counters, rest, s);
     // scratch: rest ids [n], long queue [n] of int2, counters; for the sorted schedules also
     // the sort keys / permutation double buffers [4][n], per-query (query, site) pairs and long
@@ -696,8 +713,10 @@ int run_query(p2m_index* h, MeshData& m, const float* d_pts, int64_t n, float* d
             k_query_thread<true><<<blocks, threads, 0, s>>>(v, d_pts, n, d_dist, d_closest, d_tri, d_bary, d_rest, d_cnt,
                                                             d_long, d_cnt + 1, counters, qs, cand, flag, rec);
         } else {
+            timing_mark(h, 1, s);
             k_query_thread<false><<<blocks, threads, 0, s>>>(v, d_pts, n, d_dist, d_closest, d_tri, d_bary, d_rest, d_cnt,
                                                              d_long, d_cnt + 1, nullptr, qs, cand, flag, rec);
+            timing_mark(h, 2, s);
         }
         P2M_CUDA_TRY(cudaGetLastError());
         // order-preserving compaction of the long queries (count written on the device)

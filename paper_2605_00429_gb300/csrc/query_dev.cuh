@@ -20,20 +20,14 @@ __device__ __forceinline__ bool grid_cell(const MeshView& m, float3 q, int& cell
     return true;
 }
 
-// Nearest site among the grid cell's candidates.  IDS: read the candidates as site ids and
-// their positions from the site table (4 B per candidate, a small table that stays in cache);
-// else read the inline (x, y, z, id) candidates (one 16 B load each).
-template <bool COUNT, bool IDS = false>
+// Nearest site among the grid cell's candidates: site ids (4 B each) whose positions come
+// from the site table, which stays in cache.
+template <bool COUNT>
 __device__ __forceinline__ int nearest_site(const MeshView& m, float3 q, int cell, unsigned long long* counters) {
     const int j0 = __ldg(m.cell_off + cell), j1 = __ldg(m.cell_off + cell + 1);
     auto cand = [&](int j, int& s) {
-        if (IDS) {
-            s = __ldg(m.cell_id + j);
-            return __ldg(m.sites + s);
-        }
-        const float4 p = __ldg(m.cell_site + j);
-        s = __float_as_int(p.w);
-        return p;
+        s = __ldg(m.cell_id + j);
+        return __ldg(m.sites + s);
     };
     float bd = INFINITY, sd = INFINITY;
     int bs = -1;
@@ -152,14 +146,16 @@ __device__ __forceinline__ unsigned long long scan_list(const MeshView& m, float
 }
 
 // The same scan over a list staged in shared memory by the block (see k_query_staged):
-// entries ent[0, len), their bounding spheres sph[], full triangle records rec[][4] and the
-// list's chunk boxes cb[][3].  Returns the (d2, tri) key and the winner's (s, t) and staged
+// entries ent[0, len), their bounding spheres sph[] and full triangle records rec[][4].  A
+// staged list is short, so sorted by key and scanned with the early exit alone (chunk boxes
+// of a key-sorted list are shells around the reference point and prune little; testing them
+// measured no faster).  Returns the (d2, tri) key and the winner's (s, t) and staged
 // position (for its record).
 template <bool COUNT>
 __device__ __forceinline__ unsigned long long scan_list_staged(const MeshView& m, float3 q, int site, const int2* ent,
-                                                               const float4* sph, const float4 (*rec)[4],
-                                                               const float4 (*cb)[3], int len, float& bs, float& bt,
-                                                               int& bpos, unsigned long long* counters) {
+                                                               const float4* sph, const float4 (*rec)[4], int len,
+                                                               float& bs, float& bt, int& bpos,
+                                                               unsigned long long* counters) {
     const float4 ref = __ldg(m.refs + site);
     const float rx = q.x - ref.x, ry = q.y - ref.y, rz = q.z - ref.z;
     const float dq = sqrtf(fmaf(rx, rx, fmaf(ry, ry, rz * rz)));
@@ -167,46 +163,32 @@ __device__ __forceinline__ unsigned long long scan_list_staged(const MeshView& m
     const float dq_up = fmaf(dq, 1.0f + 9.6e-7f, m.prune_abs);
     unsigned long long best = ~0ull;
     int n_exact = 0, n_entries = 0;
-    bool done = false;
-    const int nc = (len + kChunk - 1) / kChunk;
-    for (int c = 0; c < nc && !done; ++c) {
-        {
-            const float4 lo = cb[c][0], hi = cb[c][1], nr = cb[c][2];
-            const float h = dot3(f3(nr), q);
-            const float slab = fmaxf(fmaxf(lo.w - h, h - hi.w), 0.0f);
-            if (fmaxf(box_dist2(q, f3(lo), f3(hi)), slab * slab) > bound * bound) continue;
-        }
-        const int j1 = min((c + 1) * kChunk, len);
-        for (int j = c * kChunk; j < j1; ++j) {
-            const int2 e = ent[j];
-            // staged lists are short, so sorted by key: stop once every later entry is farther
-            if (__int_as_float(e.y) > bound + dq_up) {
-                done = true;
-                break;
-            }
-            if (COUNT) ++n_entries;
-            const float4 sp = sph[j];
-            const float dx = q.x - sp.x, dy = q.y - sp.y, dz = q.z - sp.z;
-            const float lim = bound + sp.w;
-            const float dc2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
-            if (dc2 > lim * lim) continue;
-            if (tri_lower_bound2_rec(rec[j][0], rec[j][1], q, sp, dc2, 8.0f * m.prune_abs) > bound * bound) continue;
-            if (COUNT) ++n_exact;
-            TriRec T;
-            T.r0 = rec[j][0];
-            T.r1 = rec[j][1];
-            T.r2 = rec[j][2];
-            T.r3 = rec[j][3];
-            float s, t;
-            const float d2 = tri_dist2(q, T, s, t);
-            const unsigned long long key = dist_key(d2, e.x);
-            if (key < best) {
-                best = key;
-                bs = s;
-                bt = t;
-                bpos = j;
-                bound = fminf(bound, fmaf(sqrtf(d2), 1.0f + 9.6e-7f, m.prune_abs));
-            }
+    for (int j = 0; j < len; ++j) {
+        const int2 e = ent[j];
+        // every later entry's lower bound exceeds the bound too
+        if (__int_as_float(e.y) > bound + dq_up) break;
+        if (COUNT) ++n_entries;
+        const float4 sp = sph[j];
+        const float dx = q.x - sp.x, dy = q.y - sp.y, dz = q.z - sp.z;
+        const float lim = bound + sp.w;
+        const float dc2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
+        if (dc2 > lim * lim) continue;
+        if (tri_lower_bound2_rec(rec[j][0], rec[j][1], q, sp, dc2, 8.0f * m.prune_abs) > bound * bound) continue;
+        if (COUNT) ++n_exact;
+        TriRec T;
+        T.r0 = rec[j][0];
+        T.r1 = rec[j][1];
+        T.r2 = rec[j][2];
+        T.r3 = rec[j][3];
+        float s, t;
+        const float d2 = tri_dist2(q, T, s, t);
+        const unsigned long long key = dist_key(d2, e.x);
+        if (key < best) {
+            best = key;
+            bs = s;
+            bt = t;
+            bpos = j;
+            bound = fminf(bound, fmaf(sqrtf(d2), 1.0f + 9.6e-7f, m.prune_abs));
         }
     }
     if (COUNT) {

@@ -193,3 +193,18 @@ def test_schedules_agree_long_lists(p2m, schedule):
     other = _query(idx, q)
     assert np.array_equal(base[0], other[0]) and np.array_equal(base[2], other[2])
     check_parity(mesh, q[:6000], tuple(a[:6000] for a in other))
+
+
+def test_kernel_timing(p2m):
+    """p2m_set_timing / p2m_query_timing: the list-scan kernel's time lies inside the call's."""
+    import torch
+    mesh, q = W.workload_large(400_000, k=4)
+    idx = p2m.P2MIndex(mesh.verts, mesh.tris)
+    pts = torch.from_numpy(q).cuda()
+    with pytest.raises(p2m.P2MError):
+        idx.query_timing()  # timing is off
+    idx.set_timing(True)
+    idx.query(pts)
+    scan_ms, call_ms = idx.query_timing()
+    assert 0.0 < scan_ms <= call_ms
+    idx.set_timing(False)
