@@ -96,6 +96,7 @@ MeshView MeshData::view() const {
     v.refs = d_refs.as<const float4>();
     v.row_off = d_row_off.as<const int32_t>();
     v.row_ent = d_row_ent.as<const int2>();
+    v.row_sph = d_row_sph.as<const float4>();
     v.chunk_off = d_chunk_off.as<const int32_t>();
     v.cbox = d_cbox.as<const float4>();
     v.l1_off = d_l1_off.as<const int32_t>();
@@ -165,6 +166,9 @@ void timing_mark(p2m_index* h, int k, cudaStream_t s) {
 p2m_index::~p2m_index() {
     for (auto& st : streams)
         if (st) cudaStreamDestroy(st);
+    for (auto& slot : pipe_ev)
+        for (auto& e : slot)
+            if (e) cudaEventDestroy(e);
     for (auto& e : tev)
         if (e) cudaEventDestroy(e);
 }

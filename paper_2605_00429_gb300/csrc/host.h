@@ -49,11 +49,14 @@ struct p2m_index {
     p2m::DevBuf scratch_idx;   // compacted list of queries left to the BVH search
     p2m::BatchState batch;     // batched-query state (tile queue, graph)
     int device = 0;
-    // host-buffer query pipeline: kPipe streams, each with its own device buffers
+    // host-buffer query pipeline: a copy-in stream, a compute stream and a copy-out stream;
+    // kPipe buffer slots, each with its own device buffers and events (copied in, computed,
+    // copied out)
     static constexpr int kPipe = 3;
     cudaStream_t streams[kPipe] = {nullptr, nullptr, nullptr};
     p2m::DevBuf pipe[kPipe][5];    // pts, dist, closest, tri, bary
     p2m::DevBuf pipe_rest[kPipe];
+    cudaEvent_t pipe_ev[kPipe][3] = {};
     p2m::DevBuf grad_acc;      // fixed-point vertex-gradient accumulator
     // kernel timing (p2m_set_timing): events at the call's start, around its list-scan
     // kernel, and at its end

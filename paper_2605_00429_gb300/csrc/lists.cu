@@ -275,6 +275,21 @@ __global__ void k_i64_to_i32(const int64_t* __restrict__ a, int32_t* __restrict_
 // Builds the lists from the device ball table (d_balls, d_ball_off): m.d_row_off, the
 // (triangle, key) entries m.d_row_ent (short lists sorted by key), the chunk boxes and the
 // level-1 boxes.
+// Bounding spheres in list order for the entries of long lists (the warp pass then reads an
+// entry's sphere with a coalesced load instead of a gather through its triangle id).
+__global__ void k_long_spheres(const int64_t* __restrict__ row_off64, int n_sites, int long_row,
+                               const int32_t* __restrict__ row_tri, const float4* __restrict__ tsph,
+                               float4* __restrict__ row_sph) {
+    const int lane = threadIdx.x & 31;
+    const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int nwarps = (gridDim.x * blockDim.x) >> 5;
+    for (int s = warp; s < n_sites; s += nwarps) {
+        const int64_t b = row_off64[s], e = row_off64[s + 1];
+        if (e - b <= long_row) continue;
+        for (int64_t j = b + lane; j < e; j += 32) row_sph[j] = tsph[row_tri[j]];
+    }
+}
+
 // List entries as (triangle, key bits) pairs: the thread scan reads both with one 8-byte load.
 __global__ void k_pack_entries(const int32_t* __restrict__ row_tri, const float* __restrict__ row_key, int64_t nnz,
                                int2* __restrict__ row_ent) {
@@ -391,15 +406,24 @@ int build_lists(MeshData& m, const float4* d_balls, const int64_t* d_ball_off, i
             m.d_row_tri.as<int32_t>(), m.d_row_key.as<float>(), nnz, m.d_row_ent.as<int2>());
         P2M_CUDA_TRY(cudaGetLastError());
     }
-    P2M_CUDA_TRY(cudaStreamSynchronize(s));
-    m.d_row_tri.release();
-    m.d_row_key.release();
     // row statistics (Table 1 Max / Avg)
     std::vector<int64_t> c(n_sites);
     P2M_CUDA_TRY(cudaMemcpyAsync(c.data(), cnt.p, sizeof(int64_t) * n_sites, cudaMemcpyDeviceToHost, s));
     P2M_CUDA_TRY(cudaStreamSynchronize(s));
     int64_t mx = 0;
     for (int64_t x : c) mx = std::max(mx, x);
+    // spheres in list order for the long lists, when there are any
+    m.d_row_sph.release();
+    if (mx > m.long_row && nnz > 0) {
+        P2M_TRY(m.d_row_sph.alloc(sizeof(float4) * nnz));
+        k_long_spheres<<<std::max(1, std::min((n_sites + 7) / 8, sm_count() * 16)), 256, 0, s>>>(
+            off64.as<int64_t>(), n_sites, m.long_row, m.d_row_tri.as<int32_t>(), m.d_tsph.as<float4>(),
+            m.d_row_sph.as<float4>());
+        P2M_CUDA_TRY(cudaGetLastError());
+        P2M_CUDA_TRY(cudaStreamSynchronize(s));
+    }
+    m.d_row_tri.release();
+    m.d_row_key.release();
     m.stats.nnz = nnz;
     m.stats.max_row = mx;
     m.stats.avg_row = n_sites ? (double)nnz / n_sites : 0.0;

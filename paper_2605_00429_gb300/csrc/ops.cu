@@ -329,16 +329,20 @@ int p2m_query_host(p2m_index* h, const float* h_pts, int64_t n, float* h_dist, f
     constexpr int kSlots = p2m_index::kPipe;
     for (auto& st : h->streams)
         if (!st) P2M_CUDA_TRY(cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking));
+    for (auto& slot : h->pipe_ev)
+        for (auto& e : slot)
+            if (!e) P2M_CUDA_TRY(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaStream_t s_in = h->streams[0], s_run = h->streams[1], s_out = h->streams[2];
     // the pipeline starts after the caller's earlier work on `stream`
     Event ev;
     P2M_CUDA_TRY(cudaEventCreateWithFlags(&ev.e, cudaEventDisableTiming));
     P2M_CUDA_TRY(cudaEventRecord(ev.e, user));
     for (auto& st : h->streams) P2M_CUDA_TRY(cudaStreamWaitEvent(st, ev.e, 0));
-    // Chunks of ~n/k (at least 1M points) on kSlots streams: while one chunk computes, the
-    // copy engines move the previous chunk's results out and the next chunk's points in.
-    // Two chunks by default: a chunk's Morton order only groups its own points, so smaller
-    // chunks put fewer queries in each grid cell and cost more per query (10M points in
-    // 1 / 2 / 4 / 8 chunks: 4.73 / 3.86 / 4.04 / 4.64 ms end to end).
+    // Chunks of ~n/k points (at least 1M): chunk c's points go in on the copy-in stream, its
+    // query runs on the compute stream, its results go out on the copy-out stream.  The
+    // chunks' kernels run one after another, so chunk c's results leave while chunk c+1
+    // computes and chunk c+2's points arrive.  A buffer slot is reused once its previous
+    // chunk's results are out.
     const int64_t k_chunks = h->params.pipe_chunks > 0 ? h->params.pipe_chunks : 3;
     const int64_t chunk = std::min<int64_t>(n, std::max<int64_t>((int64_t)1 << 20, (n + k_chunks - 1) / k_chunks));
     for (int k = 0; k < kSlots; ++k) {
@@ -348,20 +352,28 @@ int p2m_query_host(p2m_index* h, const float* h_pts, int64_t n, float* h_dist, f
         if (h_tri) P2M_TRY(h->pipe[k][3].ensure(sizeof(int32_t) * chunk));
         if (h_bary) P2M_TRY(h->pipe[k][4].ensure(sizeof(float) * 3 * chunk));
     }
-    int slot = 0;
-    for (int64_t b = 0; b < n; b += chunk, slot = (slot + 1) % kSlots) {
+    int64_t ci = 0;
+    for (int64_t b = 0; b < n; b += chunk, ++ci) {
+        const int slot = (int)(ci % kSlots);
         const int64_t c = std::min(chunk, n - b);
-        cudaStream_t s = h->streams[slot];
         DevBuf* P = h->pipe[slot];
-        P2M_CUDA_TRY(cudaMemcpyAsync(P[0].p, h_pts + 3 * b, sizeof(float) * 3 * c, cudaMemcpyHostToDevice, s));
+        cudaEvent_t* E = h->pipe_ev[slot];  // [0] copied in, [1] computed, [2] copied out
+        if (ci >= kSlots) P2M_CUDA_TRY(cudaStreamWaitEvent(s_in, E[2], 0));
+        P2M_CUDA_TRY(cudaMemcpyAsync(P[0].p, h_pts + 3 * b, sizeof(float) * 3 * c, cudaMemcpyHostToDevice, s_in));
+        P2M_CUDA_TRY(cudaEventRecord(E[0], s_in));
+        P2M_CUDA_TRY(cudaStreamWaitEvent(s_run, E[0], 0));
+        if (ci >= kSlots) P2M_CUDA_TRY(cudaStreamWaitEvent(s_run, E[2], 0));
         P2M_TRY(run_query(h, m, P[0].as<float>(), c, P[1].as<float>(), h_closest ? P[2].as<float>() : nullptr,
                           h_tri ? P[3].as<int32_t>() : nullptr, h_bary ? P[4].as<float>() : nullptr, nullptr,
-                          h->pipe_rest[slot], s));
-        P2M_CUDA_TRY(cudaMemcpyAsync(h_dist + b, P[1].p, sizeof(float) * c, cudaMemcpyDeviceToHost, s));
+                          h->pipe_rest[slot], s_run));
+        P2M_CUDA_TRY(cudaEventRecord(E[1], s_run));
+        P2M_CUDA_TRY(cudaStreamWaitEvent(s_out, E[1], 0));
+        P2M_CUDA_TRY(cudaMemcpyAsync(h_dist + b, P[1].p, sizeof(float) * c, cudaMemcpyDeviceToHost, s_out));
         if (h_closest)
-            P2M_CUDA_TRY(cudaMemcpyAsync(h_closest + 3 * b, P[2].p, sizeof(float) * 3 * c, cudaMemcpyDeviceToHost, s));
-        if (h_tri) P2M_CUDA_TRY(cudaMemcpyAsync(h_tri + b, P[3].p, sizeof(int32_t) * c, cudaMemcpyDeviceToHost, s));
-        if (h_bary) P2M_CUDA_TRY(cudaMemcpyAsync(h_bary + 3 * b, P[4].p, sizeof(float) * 3 * c, cudaMemcpyDeviceToHost, s));
+            P2M_CUDA_TRY(cudaMemcpyAsync(h_closest + 3 * b, P[2].p, sizeof(float) * 3 * c, cudaMemcpyDeviceToHost, s_out));
+        if (h_tri) P2M_CUDA_TRY(cudaMemcpyAsync(h_tri + b, P[3].p, sizeof(int32_t) * c, cudaMemcpyDeviceToHost, s_out));
+        if (h_bary) P2M_CUDA_TRY(cudaMemcpyAsync(h_bary + 3 * b, P[4].p, sizeof(float) * 3 * c, cudaMemcpyDeviceToHost, s_out));
+        P2M_CUDA_TRY(cudaEventRecord(E[2], s_out));
     }
     for (auto& st : h->streams) P2M_CUDA_TRY(cudaStreamSynchronize(st));
     return check_status_word(h, h->streams[0], "query");

@@ -99,6 +99,7 @@ struct MeshView {
     // [nnz] (triangle, key bits), key = ||ref - c_f|| - r_f; lists of <= long_row entries
     // are sorted by key
     const int2* row_ent;
+    const float4* row_sph;  // [nnz] the entries' bounding spheres in list order (long lists only), or NULL
     const int32_t* chunk_off;  // [S+1] first 32-entry chunk of each list
     const float4* cbox;     // [n_chunks][3] chunk bounds: (lo, hmin), (hi, hmax), (unit normal, 0)
     const int32_t* l1_off;  // [S+1] first level-1 box (32 chunks = 1024 entries) of each list
@@ -135,7 +136,7 @@ struct MeshData {
     DevBuf d_snorm, d_vnorm;     // pseudonormals for the sign: [T][4] (face, edges 01/12/20), [V]
     std::vector<int32_t> orig;   // host copy of d_orig
     Bvh bvh;
-    DevBuf d_sites, d_refs, d_row_off, d_row_tri, d_row_key, d_row_ent, d_cell_off, d_cell_id, d_chunk_off, d_cbox, d_l1_off, d_l1box;
+    DevBuf d_sites, d_refs, d_row_off, d_row_tri, d_row_key, d_row_ent, d_row_sph, d_cell_off, d_cell_id, d_chunk_off, d_cbox, d_l1_off, d_l1box;
     int64_t nnz = 0, n_chunks = 0;
     int long_row = 256;
     bool sorted = true;          // process queries in grid-cell Morton order

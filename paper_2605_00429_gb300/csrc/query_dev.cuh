@@ -267,8 +267,9 @@ __device__ __forceinline__ bool warp_scan_list(const MeshView& m, float3 q, int 
         float s = 0.0f, t = 0.0f;
         if (j < min(r0 + (c + 1) * kChunk, r1)) {
             if (COUNT) ++n_entries;
+            // the sphere in list order when the list has it (a coalesced load beside the id)
             const int f = __ldg(&m.row_ent[j].x);
-            const float4 sp = __ldg(m.tsph + f);
+            const float4 sp = m.row_sph ? __ldg(m.row_sph + j) : __ldg(m.tsph + f);
             const float dx = q.x - sp.x, dy = q.y - sp.y, dz = q.z - sp.z;
             const float lim = bound + sp.w;
             const float dc2 = fmaf(dx, dx, fmaf(dy, dy, dz * dz));
