@@ -6,12 +6,14 @@
 // build slack plus the FP32 rounding of the centre, so a triangle whose FP64 distance to a
 // ball is <= r joins the list (the test is solid ball vs solid triangle).
 //
-// One warp per site; lanes split the site's balls.  The warp walks the BVH in lockstep
-// (the traversal stack is warp-uniform); a node is entered if any lane's ball overlaps the
-// node box, a triangle is kept if any lane's ball reaches it.  Two passes share the code:
-// count, then (after a scan) fill.  Both passes visit triangles in the same order.
+// One warp per (site, subtree) work item; lanes split the site's balls.  The warp walks the
+// subtree in lockstep (the traversal stack is warp-uniform); a node is entered if any lane's
+// ball overlaps the node box, a triangle is kept if any lane's ball reaches it.  Two passes
+// share the code: count, then (after a scan) fill.  Both passes visit triangles in the same
+// order.
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 
 #include <cub/device/device_scan.cuh>
 #include <cub/device/device_segmented_sort.cuh>
@@ -44,21 +46,28 @@ __device__ __forceinline__ bool any_ball_tri(const float4* __restrict__ balls, i
     return __any_sync(0xffffffffu, hit);
 }
 
+// Work items: (site, subtree).  The BVH is cut at a fixed depth into subtrees, listed left to
+// right as (parent node, child 0 or 1); a site's list is the concatenation of its items in that
+// order, so one warp never walks the whole tree for a site whose balls cover most of the mesh
+// (the cells reaching the corners of D), and such a site's work spreads over its items' warps.
 template <bool FILL>
 __global__ void __launch_bounds__(32 * kListWarps) k_lists(const float4* __restrict__ balls, const int64_t* __restrict__ ball_off,
                                                             int n_sites, const BNode* __restrict__ nodes, int root,
+                                                            const int2* __restrict__ subroots, int n_sub,
                                                             const float4* __restrict__ tri, int64_t* __restrict__ count,
-                                                            const int64_t* __restrict__ row_off64, int32_t* __restrict__ row_tri,
+                                                            const int64_t* __restrict__ item_off, int32_t* __restrict__ row_tri,
                                                             unsigned* status) {
     __shared__ int stk[kListWarps][kListStack];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = gridDim.x * kListWarps;
-    for (int s = blockIdx.x * kListWarps + w; s < n_sites; s += nwarps) {
+    const int64_t n_items = (int64_t)n_sites * n_sub;
+    for (int64_t it = (int64_t)blockIdx.x * kListWarps + w; it < n_items; it += nwarps) {
+        const int s = (int)(it / n_sub), r = (int)(it % n_sub);
         const int64_t b0 = ball_off[s];
         const int nb = (int)(ball_off[s + 1] - b0);
         const float4* sb = balls + b0;
         int64_t k = 0;
-        int64_t out = FILL ? row_off64[s] : 0;
+        const int64_t out = FILL ? item_off[it] : 0;
         auto emit = [&](int f) {
             if (FILL && lane == 0) row_tri[out + k] = f;
             ++k;
@@ -68,8 +77,21 @@ __global__ void __launch_bounds__(32 * kListWarps) k_lists(const float4* __restr
                 const TriRec T = load_tri(tri, ~root);
                 if (any_ball_tri(sb, nb, T)) emit(~root);
             } else {
+                // the item's subtree: child `which` of node `parent`, tested by its box first
+                const int2 sr = __ldg(subroots + r);
+                const float4* pp = reinterpret_cast<const float4*>(nodes + sr.x) + 2 * sr.y;
+                const float4 rlo = __ldg(pp), rhi = __ldg(pp + 1);
+                const int rc = __float_as_int(rlo.w);
+                int node = -1;
+                if (any_ball_box(sb, nb, f3(rlo), f3(rhi))) {
+                    if (rc < 0) {
+                        const TriRec T = load_tri(tri, ~rc);
+                        if (any_ball_tri(sb, nb, T)) emit(~rc);
+                    } else {
+                        node = rc;
+                    }
+                }
                 int sp = 0;
-                int node = root;
                 while (node >= 0) {
                     const float4* np = reinterpret_cast<const float4*>(nodes + node);
                     const float4 lo0 = __ldg(np), hi0 = __ldg(np + 1), lo1 = __ldg(np + 2), hi1 = __ldg(np + 3);
@@ -112,9 +134,15 @@ __global__ void __launch_bounds__(32 * kListWarps) k_lists(const float4* __restr
                 }
             }
         }
-        if (!FILL && lane == 0) count[s] = k;
-        if (FILL && lane == 0 && k != row_off64[s + 1] - row_off64[s]) atomicOr(status, ST_BAD);
+        if (!FILL && lane == 0) count[it] = k;
+        if (FILL && lane == 0 && k != item_off[it + 1] - item_off[it]) atomicOr(status, ST_BAD);
     }
+}
+
+// Site offsets from the item offsets: off64[s] = item_off[s * n_sub].
+__global__ void k_site_offsets(const int64_t* __restrict__ item_off, int n_sites, int n_sub, int64_t* __restrict__ off64) {
+    for (int s = blockIdx.x * blockDim.x + threadIdx.x; s <= n_sites; s += gridDim.x * blockDim.x)
+        off64[s] = item_off[(int64_t)s * n_sub];
 }
 
 // Chunks of 32 consecutive list entries, each with the bounding box of its triangles
@@ -299,19 +327,62 @@ __global__ void k_pack_entries(const int32_t* __restrict__ row_tri, const float*
 
 int build_lists(MeshData& m, const float4* d_balls, const int64_t* d_ball_off, int n_sites, unsigned* status,
                 cudaStream_t s) {
-    DevBuf cnt, off64, tmp;
-    P2M_TRY(cnt.alloc(sizeof(int64_t) * (n_sites + 1)));
-    P2M_TRY(off64.alloc(sizeof(int64_t) * (n_sites + 1)));
-    const int blocks = std::max(1, std::min((n_sites + kListWarps - 1) / kListWarps, sm_count() * 16));
     const MeshView v = m.view();
-    k_lists<false><<<blocks, 32 * kListWarps, 0, s>>>(d_balls, d_ball_off, n_sites, v.bvh, v.bvh_root, v.tri,
-                                                     cnt.as<int64_t>(), nullptr, nullptr, status);
+    // the subtrees of the work items: the children of the nodes at depth kSplitDepth - 1 (a
+    // leaf met earlier stands for itself), left to right
+    constexpr int kSplitDepth = 4;
+    auto child_ref = [](float w) {
+        int r;
+        std::memcpy(&r, &w, sizeof(r));
+        return r;
+    };
+    std::vector<int2> sub;
+    if (v.bvh_root >= 0) {
+        std::vector<int2> level = {make_int2(-1, v.bvh_root)};  // (parent, node) with parent -1: the root
+        for (int d = 0; d < kSplitDepth; ++d) {
+            std::vector<int2> nextl;
+            for (const int2& e : level) {
+                if (e.y < 0) {  // a leaf: keep it where it is
+                    nextl.push_back(e);
+                    continue;
+                }
+                BNode nd;
+                P2M_CUDA_TRY(cudaMemcpy(&nd, v.bvh + e.y, sizeof(BNode), cudaMemcpyDeviceToHost));
+                nextl.push_back(make_int2(e.y, child_ref(nd.lo0.w)));
+                nextl.push_back(make_int2(e.y, child_ref(nd.lo1.w)));
+            }
+            level.swap(nextl);
+        }
+        // (parent, child slot): which child of the parent each subtree root is
+        for (const int2& e : level) {
+            BNode nd;
+            P2M_CUDA_TRY(cudaMemcpy(&nd, v.bvh + e.x, sizeof(BNode), cudaMemcpyDeviceToHost));
+            sub.push_back(make_int2(e.x, child_ref(nd.lo0.w) == e.y ? 0 : 1));
+        }
+    } else {
+        sub.push_back(make_int2(0, 0));  // one triangle: the root is the leaf itself
+    }
+    const int n_sub = (int)sub.size();
+    const int64_t n_items = (int64_t)n_sites * n_sub;
+    DevBuf d_sub, cnt, item_off, off64, tmp;
+    P2M_TRY(d_sub.alloc(sizeof(int2) * n_sub));
+    P2M_CUDA_TRY(cudaMemcpyAsync(d_sub.p, sub.data(), sizeof(int2) * n_sub, cudaMemcpyHostToDevice, s));
+    P2M_TRY(cnt.alloc(sizeof(int64_t) * (n_items + 1)));
+    P2M_TRY(item_off.alloc(sizeof(int64_t) * (n_items + 1)));
+    P2M_TRY(off64.alloc(sizeof(int64_t) * (n_sites + 1)));
+    const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n_items + kListWarps - 1) / kListWarps,
+                                                                   (int64_t)sm_count() * 16));
+    k_lists<false><<<blocks, 32 * kListWarps, 0, s>>>(d_balls, d_ball_off, n_sites, v.bvh, v.bvh_root, d_sub.as<int2>(),
+                                                     n_sub, v.tri, cnt.as<int64_t>(), nullptr, nullptr, status);
     P2M_CUDA_TRY(cudaGetLastError());
-    P2M_CUDA_TRY(cudaMemsetAsync(cnt.as<int64_t>() + n_sites, 0, sizeof(int64_t), s));
+    P2M_CUDA_TRY(cudaMemsetAsync(cnt.as<int64_t>() + n_items, 0, sizeof(int64_t), s));
     size_t tb = 0;
-    P2M_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, tb, cnt.as<int64_t>(), off64.as<int64_t>(), n_sites + 1, s));
+    P2M_CUDA_TRY(cub::DeviceScan::ExclusiveSum(nullptr, tb, cnt.as<int64_t>(), item_off.as<int64_t>(), n_items + 1, s));
     P2M_TRY(tmp.alloc(tb + 16));
-    P2M_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp.p, tb, cnt.as<int64_t>(), off64.as<int64_t>(), n_sites + 1, s));
+    P2M_CUDA_TRY(cub::DeviceScan::ExclusiveSum(tmp.p, tb, cnt.as<int64_t>(), item_off.as<int64_t>(), n_items + 1, s));
+    k_site_offsets<<<std::max(1, std::min((n_sites + 256) / 256, 4096)), 256, 0, s>>>(item_off.as<int64_t>(), n_sites,
+                                                                                     n_sub, off64.as<int64_t>());
+    P2M_CUDA_TRY(cudaGetLastError());
     int64_t nnz = 0;
     P2M_CUDA_TRY(cudaMemcpyAsync(&nnz, off64.as<int64_t>() + n_sites, sizeof(int64_t), cudaMemcpyDeviceToHost, s));
     P2M_CUDA_TRY(cudaStreamSynchronize(s));
@@ -321,8 +392,9 @@ int build_lists(MeshData& m, const float4* d_balls, const int64_t* d_ball_off, i
     m.nnz = nnz;
     P2M_TRY(m.d_row_tri.alloc(sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
     P2M_TRY(m.d_row_off.alloc(sizeof(int32_t) * (n_sites + 1)));
-    k_lists<true><<<blocks, 32 * kListWarps, 0, s>>>(d_balls, d_ball_off, n_sites, v.bvh, v.bvh_root, v.tri, nullptr,
-                                                    off64.as<int64_t>(), m.d_row_tri.as<int32_t>(), status);
+    k_lists<true><<<blocks, 32 * kListWarps, 0, s>>>(d_balls, d_ball_off, n_sites, v.bvh, v.bvh_root, d_sub.as<int2>(),
+                                                    n_sub, v.tri, nullptr, item_off.as<int64_t>(),
+                                                    m.d_row_tri.as<int32_t>(), status);
     P2M_CUDA_TRY(cudaGetLastError());
     k_i64_to_i32<<<64, 256, 0, s>>>(off64.as<int64_t>(), m.d_row_off.as<int32_t>(), n_sites + 1);
     P2M_CUDA_TRY(cudaGetLastError());
@@ -407,11 +479,11 @@ int build_lists(MeshData& m, const float4* d_balls, const int64_t* d_ball_off, i
         P2M_CUDA_TRY(cudaGetLastError());
     }
     // row statistics (Table 1 Max / Avg)
-    std::vector<int64_t> c(n_sites);
-    P2M_CUDA_TRY(cudaMemcpyAsync(c.data(), cnt.p, sizeof(int64_t) * n_sites, cudaMemcpyDeviceToHost, s));
+    std::vector<int64_t> c(n_sites + 1);
+    P2M_CUDA_TRY(cudaMemcpyAsync(c.data(), off64.p, sizeof(int64_t) * (n_sites + 1), cudaMemcpyDeviceToHost, s));
     P2M_CUDA_TRY(cudaStreamSynchronize(s));
     int64_t mx = 0;
-    for (int64_t x : c) mx = std::max(mx, x);
+    for (int i = 0; i < n_sites; ++i) mx = std::max(mx, c[i + 1] - c[i]);
     // spheres in list order for the long lists, when there are any
     m.d_row_sph.release();
     if (mx > m.long_row && nnz > 0) {
