@@ -241,6 +241,7 @@ def config_leg(p2m, key, dev, steps, schedule, flush, hbm_peak):
             "steps": steps, "build_wall_ms": build_ms, "csr_build_ms": st["ms_tri"] + st["ms_lbvh"] + st["ms_k1"],
             "grid_build_ms": st["ms_grid"], "sites": st["n_sites"], "aux_sites": st["n_aux_sites"],
             "avg_list": st["avg_row"], "max_list": st["max_row"],
+            "queried_list": cnt["queried_list"] / n,
             "queried_entries": cnt["row_entries"] / n, "queried_exact": cnt["exact_tests"] / n,
             "hbm_frac": BYTES_PER_QUERY * n / (ms / 1e3) / 1e9 / hbm_peak}
 
@@ -323,7 +324,8 @@ def run_ablation(args):
             ms = e0.elapsed_time(e1) / 5
             print(json.dumps({"ablation": desc, "aux": label, "build_ms": build_ms, "query_ms": ms,
                               "queries_per_s": len(q) / (ms / 1e3), "max_list": st["max_row"],
-                              "avg_list": st["avg_row"], "queried_entries": c["row_entries"] / len(q),
+                              "avg_list": st["avg_row"], "queried_list": c["queried_list"] / len(q),
+                              "queried_entries": c["row_entries"] / len(q),
                               "queried_exact": c["exact_tests"] / len(q), "long_queries": c["long_queries"],
                               "sites": st["n_sites"], "aux_sites": st["n_aux_sites"], "nnz": st["nnz"]}), flush=True)
             del idx
@@ -463,7 +465,8 @@ def main():
                       "sites": st["n_sites"], "aux_sites": st["n_aux_sites"], "nnz": st["nnz"],
                       "max_list": st["max_row"], "avg_list": st["avg_row"], "grid": st["grid_res"],
                       "grid_entries": st["grid_entries"], "grid_max": st["grid_max"]},
-            "counters": {"queried_entries": cnt["row_entries"] / n, "queried_exact": cnt["exact_tests"] / n,
+            "counters": {"queried_list": cnt["queried_list"] / n,
+                         "queried_entries": cnt["row_entries"] / n, "queried_exact": cnt["exact_tests"] / n,
                          "sites_per_query": cnt["site_candidates"] / n, "outside": cnt["n_outside"],
                          "tie_rechecks": cnt["tie_rechecks"], "long_queries": cnt["long_queries"],
                          "long_entries_per_long_query": cnt["long_entries"] / max(1, cnt["long_queries"])}}

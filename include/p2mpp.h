@@ -149,6 +149,9 @@ typedef struct {
     int64_t exact_tests;      /* exact point-triangle tests run (after pruning) */
     int64_t long_queries;     /* queries whose list was scanned by the warp-cooperative pass */
     int64_t long_entries;     /* list entries those queries visited (part of row_entries) */
+    int64_t queried_list;     /* sum over in-domain queries of the length of their nearest
+                                 site's list (over n_queries: the query-weighted average list
+                                 length, Table 4's "Queried") */
 } p2m_counters;
 
 /* Library version string. */

@@ -55,7 +55,7 @@ class Stats(ctypes.Structure):
 
 class Counters(ctypes.Structure):
     _fields_ = [(n, ctypes.c_int64) for n in ("n_queries", "n_outside", "site_candidates", "tie_rechecks",
-                                             "row_entries", "exact_tests", "long_queries", "long_entries")]
+                                             "row_entries", "exact_tests", "long_queries", "long_entries", "queried_list")]
 
     def as_dict(self):
         return {name: getattr(self, name) for name, _ in self._fields_}

@@ -458,6 +458,7 @@ int p2m_query_counters(p2m_index* h, const float* d_pts, int64_t n, float* d_dis
     out->exact_tests = (int64_t)c[4];
     out->long_queries = (int64_t)c[5];
     out->long_entries = (int64_t)c[6];
+    out->queried_list = (int64_t)c[7];
     return P2M_OK;
 }
 

@@ -48,6 +48,7 @@ bool Clipper::clip(const double n[3], double d, double tol) {
         val[i] = n[0] * V[3 * i] + n[1] * V[3 * i + 1] + n[2] * V[3 * i + 2] - d;
         n_out += val[i] > tol;
     }
+    cut = n_out > 0;
     if (n_out == 0) return true;
     if (n_out == nv) {
         V.clear();

@@ -179,7 +179,6 @@ __host__ __device__ int clip_site(CellPoly& C, const double* site, int s, const 
         double3 nrm = make_double3(pt.x - ps.x, pt.y - ps.y, pt.z - ps.z);
         const double d2 = nrm.x * nrm.x + nrm.y * nrm.y + nrm.z * nrm.z;
         if (0.25 * d2 > r2 * (1.0 + 1e-9) + tol * tol) break;
-        if (++used > max_clip) break;
         const double len = sqrt(d2);
         if (!(len > 0)) continue;
         nrm = make_double3(nrm.x / len, nrm.y / len, nrm.z / len);
@@ -189,7 +188,10 @@ __host__ __device__ int clip_site(CellPoly& C, const double* site, int s, const 
             st = -rc;
             break;
         }
-        if (rc == 1) r2 = cell_radius2(C, ps);
+        if (rc == 1) {
+            r2 = cell_radius2(C, ps);
+            if (++used >= max_clip) break;
+        }
     }
     if (st != CELL_OK) return st;
     int nc = 0;

@@ -60,8 +60,10 @@ struct Clipper {
     std::vector<double> V;                 // xyz
     std::vector<int> fidx, foff;           // faces as cyclic vertex-id lists (CSR)
     void box(const double lo[3], const double hi[3]);
-    // keep the half-space n . x <= d; returns false if the polytope became empty
+    // keep the half-space n . x <= d; returns false if the polytope became empty.  `cut`
+    // tells whether the last call removed a corner.
     bool clip(const double n[3], double d, double tol);
+    bool cut = false;
     double radius_from(const double p[3]) const;  // max distance from p to a corner
     double radius2_from(const double p[3]) const;  // its square
     int n_verts() const { return (int)(V.size() / 3); }

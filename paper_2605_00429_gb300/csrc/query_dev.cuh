@@ -7,7 +7,7 @@
 
 namespace p2m {
 
-enum { C_OUTSIDE = 0, C_SITES = 1, C_TIES = 2, C_ROWS = 3, C_EXACT = 4, C_LONG = 5, C_LONG_ROWS = 6 };
+enum { C_OUTSIDE = 0, C_SITES = 1, C_TIES = 2, C_ROWS = 3, C_EXACT = 4, C_LONG = 5, C_LONG_ROWS = 6, C_QUERIED = 7 };
 
 __device__ __forceinline__ bool grid_cell(const MeshView& m, float3 q, int& cell) {
     const float fx = (q.x - m.lo.x) * m.inv_h.x;
@@ -62,6 +62,8 @@ __device__ __forceinline__ int nearest_site(const MeshView& m, float3 q, int cel
         }
         bs = bi;
     }
+    if (COUNT && bs >= 0)
+        atomicAdd(counters + C_QUERIED, (unsigned long long)(__ldg(m.row_off + bs + 1) - __ldg(m.row_off + bs)));
     return bs;
 }
 

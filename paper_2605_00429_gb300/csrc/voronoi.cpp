@@ -121,9 +121,11 @@ void SiteSet::neighbour_csr() {
 // Corners of site s's cell: D cut by the bisectors of its Delaunay neighbours, nearest
 // neighbour first (the neighbour lists are kept in that order).  A neighbour t can cut the
 // cell only if its bisector, at distance |s - t| / 2 from s, comes within the cell's radius
-// about s; after kMaxClip neighbours the clip stops, and the cell is then a superset of the
-// true one, which is still a valid region for Eq. 3.  Returns false if the cell clipped to
-// nothing.
+// about s.  Only bisectors that remove a corner count towards kMaxClip: a fan centre has
+// hundreds of near neighbours whose bisectors are all faces (or redundant), and the far
+// neighbours that close its cell must still be reached.  After kMaxClip cutting bisectors
+// the clip stops, and the cell is then a superset of the true one, which is still a valid
+// region for Eq. 3.  Returns false if the cell clipped to nothing.
 bool SiteSet::clip_one(int s, const double dom_lo[3], const double dom_hi[3], double tol, Clipper& C) const {
     double ps[3];
     world(s, ps);
@@ -135,12 +137,12 @@ bool SiteSet::clip_one(int s, const double dom_lo[3], const double dom_hi[3], do
         double nrm[3] = {pt[0] - ps[0], pt[1] - ps[1], pt[2] - ps[2]};
         const double d2 = nrm[0] * nrm[0] + nrm[1] * nrm[1] + nrm[2] * nrm[2];
         if (0.25 * d2 > C.radius2_from(ps) * (1.0 + 1e-9) + tol * tol) break;
-        if (++used > kMaxClip) break;
         const double len = std::sqrt(d2);
         if (!(len > 0)) continue;
         for (double& c : nrm) c /= len;
         const double d = 0.5 * (nrm[0] * (pt[0] + ps[0]) + nrm[1] * (pt[1] + ps[1]) + nrm[2] * (pt[2] + ps[2]));
         if (!C.clip(nrm, d, tol)) return false;
+        if (C.cut && ++used >= kMaxClip) break;
     }
     return true;
 }

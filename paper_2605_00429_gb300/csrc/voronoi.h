@@ -19,7 +19,7 @@ struct SiteSet {
     std::vector<double> cell_xyz;
 
     // at most this many bisectors cut one cell (the cell is then a superset of the true one)
-    static constexpr int kMaxClip = 256;
+    static constexpr int kMaxClip = 4096;
     // clipping tolerance: a corner within this distance of a cutting plane is kept
     static double clip_tol(double diag) { return 1e-12 * diag; }
 

@@ -26,7 +26,11 @@ def _cases():
     ico = W.icosphere(2).verts
     g = np.stack(np.meshgrid(*[np.arange(4.0)] * 3, indexing="ij"), -1).reshape(-1, 3) / 3 - 0.5
     cyl = W.cylinder_cone(24, 6, 3, 2).verts
+    # fan centres (cap centre, cone apex) with 300 neighbours each: their cells are closed by
+    # far neighbours only after hundreds of near ones have cut them
+    fan = W.cylinder_cone(300, 4, 2, 2).verts
     return {
+        "cylinder_fan300": fan,
         "random": (rng.random((300, 3)) - 0.5).astype(np.float32),
         "uv_sphere": uv,
         "icosphere": ico,
