@@ -299,9 +299,11 @@ def run_ablation(args):
          lambda: W.workload_symmetric(1_000_000)),
     ]
     # (label, build parameters): no augmentation, augmentation with the single Eq. 8 ball per
-    # auxiliary site, augmentation with its per-corner balls (the default)
+    # auxiliary site, augmentation with its per-corner balls (the default), and the same with
+    # each centre site at its tau-cell's centre instead of its Voronoi vertices' centroid
     modes = [("off", dict(enable_aux=0)), ("on, Eq. 8 ball", dict(enable_aux=1, aux_balls=0)),
-             ("on, corner balls", dict(enable_aux=1, aux_balls=1))]
+             ("on, corner balls", dict(enable_aux=1, aux_balls=1)),
+             ("on, corner balls, p_c at the cell centre", dict(enable_aux=1, aux_balls=1, aux_centre=0))]
     for desc, make in cases:
         mesh, q = make()
         if q is None:

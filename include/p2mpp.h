@@ -65,7 +65,7 @@ typedef struct {
     float domain_scale;
     /* Site augmentation of Section 3.2 on/off [1]. */
     int enable_aux;
-    /* tau = tau_scale x mean edge length [2.0] (Section 3.2 "Choice of Parameters"). */
+    /* tau = tau_scale x mean edge length [1.0] (Section 3.2 "Choice of Parameters"). */
     float tau_scale;
     /* A tau-cell is dense when its Voronoi-vertex count exceeds density_factor x the median
      * count of non-empty tau-cells [8.0] and density_min [256].  (Symmetric meshes put
@@ -74,7 +74,8 @@ typedef struct {
     int density_min;
     /* Auxiliary sites per ring: 12 (icosahedron directions) or 6 (octahedron) [12]. */
     int ring_sites;
-    /* Ring radius = ring_radius_scale x tau [1.299 = 0.75 sqrt 3]. */
+    /* Ring radius = ring_radius_scale x tau [0.9: just above sqrt(3) / 2, the radius of the
+     * sphere about a tau-cell's centre that encloses the cell]. */
     float ring_radius_scale;
     /* List-membership slack, relative to the bbox diagonal [1e-6]: a triangle joins a list
      * when its distance to a ball is <= radius + slack (conservative). */
@@ -83,7 +84,7 @@ typedef struct {
     int nn_grid_res;
     /* Query schedule [5]: 5 = queries counting-sorted by nearest site, then each block stages
      * the short lists of the sites of its 1024 queries (entries, bounding spheres, triangle
-     * records, chunk boxes) in shared memory and scans them thread per query; lists longer
+     * records) in shared memory and scans them thread per query; lists longer
      * than long_list take a warp-cooperative best-first scan (a call with fewer than 48
      * queries per site takes schedule 0 instead); 0 = queries sorted by the Morton code of
      * their grid cell, then thread per query for lists up to long_list entries and the
@@ -112,6 +113,10 @@ typedef struct {
      * contains the corner balls (triangle inequality), so both give exact results; the corner
      * balls give shorter lists where the cell is large. */
     int aux_balls;
+    /* Position of the centre site p_c of a dense tau-cell [1]: 1 = the centroid of the
+     * Voronoi vertices binned into the cell (the cluster the site is meant to isolate);
+     * 0 = the geometric centre of the tau-cell. */
+    int aux_centre;
 } p2m_build_params;
 
 /* Build statistics (Section 4.1, Table 1: Max / Avg list length) and stage timings. */

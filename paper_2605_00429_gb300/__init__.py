@@ -31,7 +31,7 @@ class BuildParams(ctypes.Structure):
                 ("ring_radius_scale", ctypes.c_float), ("build_eps_rel", ctypes.c_float),
                 ("nn_grid_res", ctypes.c_int), ("schedule", ctypes.c_int), ("deterministic", ctypes.c_int),
                 ("seed", ctypes.c_int), ("long_list", ctypes.c_int), ("gpu_cells", ctypes.c_int),
-                ("pipe_chunks", ctypes.c_int), ("aux_balls", ctypes.c_int)]
+                ("pipe_chunks", ctypes.c_int), ("aux_balls", ctypes.c_int), ("aux_centre", ctypes.c_int)]
 
 
 class Stats(ctypes.Structure):

@@ -187,6 +187,7 @@ static int validate_params(const p2m_build_params& p) {
     if (p.long_list < 0) return fail(P2M_ERR_INVALID_ARG, "long_list must be >= 0");
     if (p.pipe_chunks < 0) return fail(P2M_ERR_INVALID_ARG, "pipe_chunks must be >= 0");
     if (p.aux_balls != 0 && p.aux_balls != 1) return fail(P2M_ERR_INVALID_ARG, "aux_balls must be 0 or 1");
+    if (p.aux_centre != 0 && p.aux_centre != 1) return fail(P2M_ERR_INVALID_ARG, "aux_centre must be 0 or 1");
     return P2M_OK;
 }
 
@@ -369,11 +370,11 @@ int p2m_default_params(p2m_build_params* out) {
     std::memset(out, 0, sizeof(*out));
     out->domain_scale = 1.5f;
     out->enable_aux = 1;
-    out->tau_scale = 2.0f;
+    out->tau_scale = 1.0f;
     out->density_factor = 8.0f;
     out->density_min = 256;
     out->ring_sites = 12;
-    out->ring_radius_scale = 1.299038f;  // 0.75 * sqrt(3)
+    out->ring_radius_scale = 0.9f;  // just above sqrt(3) / 2
     out->build_eps_rel = 1e-6f;
     out->nn_grid_res = 0;
     out->schedule = 5;
@@ -381,6 +382,7 @@ int p2m_default_params(p2m_build_params* out) {
     out->seed = 1;
     out->gpu_cells = 1;
     out->aux_balls = 1;
+    out->aux_centre = 1;
     return P2M_OK;
 }
 

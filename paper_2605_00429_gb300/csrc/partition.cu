@@ -115,8 +115,9 @@ struct PointHash {
 };
 
 // Section 3.2: bin the Voronoi vertices into a tau-grid, flag dense cells, and add a centre
-// site plus a ring of auxiliary sites on an enclosing sphere for each; ring sites that fall
-// near an existing site or inside another flagged cell's bounding sphere are dropped.
+// site p_c (the centroid of the cell's Voronoi vertices, or the cell's centre) plus a ring
+// of auxiliary sites on a sphere about p_c for each; sites that fall near an existing site,
+// and ring sites that fall inside a neighbouring dense cell's ring, are dropped.
 // Returns the number of auxiliary sites appended to ss.pts.
 static int augment(SiteSet& ss, MeshData& m, const p2m_build_params& prm, int64_t& n_dense, cudaStream_t s) {
     n_dense = 0;
@@ -171,16 +172,41 @@ static int augment(SiteSet& ss, MeshData& m, const p2m_build_params& prm, int64_
     m.stats.aug_cell_median = (int64_t)median;
     m.stats.aug_cell_max = *std::max_element(vals.begin(), vals.end());
     const double thresh = std::max((double)prm.density_min, prm.density_factor * median);
-    std::vector<std::array<double, 3>> centres;
+    // dense cells: (geometric centre of the tau-cell, position of p_c)
+    std::unordered_map<uint64_t, int> dense_id;
+    std::vector<std::array<double, 6>> dense;
     for (size_t j = 0; j < cell_key.size(); ++j) {
         if (cell_count[j] <= thresh) continue;
         const uint64_t k = cell_key[j];
         const int64_t cx = (int64_t)(k % ncx), cy = (int64_t)((k / ncx) % ncy), cz = (int64_t)(k / ((uint64_t)ncx * ncy));
-        centres.push_back({m.dom_lo[0] + (cx + 0.5) * tau, m.dom_lo[1] + (cy + 0.5) * tau, m.dom_lo[2] + (cz + 0.5) * tau});
+        const double g[3] = {m.dom_lo[0] + (cx + 0.5) * tau, m.dom_lo[1] + (cy + 0.5) * tau,
+                             m.dom_lo[2] + (cz + 0.5) * tau};
+        dense_id[k] = (int)dense.size();
+        dense.push_back({g[0], g[1], g[2], g[0], g[1], g[2]});
     }
-    std::sort(centres.begin(), centres.end());
-    n_dense = (int64_t)centres.size();
-    if (centres.empty()) return 0;
+    n_dense = (int64_t)dense.size();
+    if (dense.empty()) return 0;
+    if (prm.aux_centre) {
+        // p_c at the centroid of the Voronoi vertices the cell holds (the same binning as above)
+        std::vector<double> sum(4 * dense.size(), 0.0);
+        for (size_t i = 0; i + 2 < cc.size(); i += 3) {
+            const double* w = &cc[i];
+            bool in = true;
+            for (int k = 0; k < 3; ++k) in &= w[k] >= m.dom_lo[k] && w[k] <= m.dom_hi[k];
+            if (!in) continue;
+            int64_t c[3];
+            for (int k = 0; k < 3; ++k) c[k] = (int64_t)std::floor((w[k] - m.dom_lo[k]) / tau);
+            auto it = dense_id.find((uint64_t)((c[2] * ncy + c[1]) * ncx + c[0]));
+            if (it == dense_id.end()) continue;
+            double* sm = &sum[4 * (size_t)it->second];
+            for (int k = 0; k < 3; ++k) sm[k] += w[k];
+            sm[3] += 1.0;
+        }
+        for (size_t j = 0; j < dense.size(); ++j)
+            if (sum[4 * j + 3] > 0)
+                for (int k = 0; k < 3; ++k) dense[j][3 + k] = sum[4 * j + k] / sum[4 * j + 3];
+    }
+    std::sort(dense.begin(), dense.end());
     PointHash sites;
     sites.cell = std::max(tau, 1e-30);
     for (int i = 0; i < (int)ss.pts.size(); ++i) {
@@ -190,7 +216,7 @@ static int augment(SiteSet& ss, MeshData& m, const p2m_build_params& prm, int64_
     }
     PointHash flagged;
     flagged.cell = tau;
-    for (auto& c : centres) flagged.add(c.data());
+    for (auto& c : dense) flagged.add(c.data());
     const double ring_r = prm.ring_radius_scale * tau;
     const double bound_r = 0.5 * std::sqrt(3.0) * tau;  // a flagged cell's bounding sphere
     const std::vector<double> dirs = ring_dirs(prm.ring_sites);
@@ -198,20 +224,37 @@ static int augment(SiteSet& ss, MeshData& m, const p2m_build_params& prm, int64_
     auto try_add = [&](const double* p) {
         bool in = true;
         for (int k = 0; k < 3; ++k) in &= p[k] > m.dom_lo[k] && p[k] < m.dom_hi[k];
-        if (!in || sites.near(p, 0.5 * tau)) return;
+        if (!in || sites.near(p, 0.5 * tau)) return false;
         const IPt q = ss.lat.to_lattice(p);
-        if (!ss.lat.inside(q)) return;
+        if (!ss.lat.inside(q)) return false;
         ss.pts.push_back(q);
         sites.add(p);
         ++added;
+        return true;
     };
-    for (auto& c : centres) try_add(c.data());
-    for (auto& c : centres)
+    // the centre sites (a centroid within half a cell of a site already placed is dropped:
+    // clusters that straddle cell faces give neighbouring cells nearly the same centroid)
+    std::vector<char> placed(dense.size(), 0);
+    PointHash centres;
+    centres.cell = std::max(ring_r, 1e-30);
+    for (size_t j = 0; j < dense.size(); ++j)
+        if (try_add(dense[j].data() + 3)) {
+            placed[j] = 1;
+            centres.add(dense[j].data() + 3);
+        }
+    for (size_t j = 0; j < dense.size(); ++j) {
+        const auto& c = dense[j];
+        // with the cells' centres, a ring site inside another flagged cell's bounding sphere is
+        // dropped; with centroids, a ring site closer to another centre site than the ring
+        // radius is (it lies inside that site's ring).  Either way the rings of adjacent dense
+        // cells merge into one around them.
+        if (prm.aux_centre && !placed[j]) continue;
         for (size_t d = 0; d < dirs.size(); d += 3) {
-            const double p[3] = {c[0] + ring_r * dirs[d], c[1] + ring_r * dirs[d + 1], c[2] + ring_r * dirs[d + 2]};
-            if (flagged.near(p, bound_r)) continue;  // merged ring of adjacent flagged cells
+            const double p[3] = {c[3] + ring_r * dirs[d], c[4] + ring_r * dirs[d + 1], c[5] + ring_r * dirs[d + 2]};
+            if (prm.aux_centre ? centres.near(p, ring_r * (1.0 - 1e-6)) : flagged.near(p, bound_r)) continue;
             try_add(p);
         }
+    }
     return added;
 }
 

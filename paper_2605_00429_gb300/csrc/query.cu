@@ -72,9 +72,9 @@ __global__ void __launch_bounds__(256, 6) k_query_thread(MeshView m, const float
 
 // ---------------------------------------------------------------------------------------
 // Site-staged schedule (5).  The queries are counting-sorted by their nearest site, so that
-// runs of consecutive queries share one interception list; a block of 256 queries stages the
-// short lists of its runs (entries, bounding spheres, full triangle records, chunk boxes) in
-// shared memory once, and every thread then scans its list from there.  The lanes of a warp
+// runs of consecutive queries share one interception list; a block of 256 threads takes a
+// tile of up to 1024 queries, stages the short lists of its runs (entries, bounding spheres,
+// full triangle records) in shared memory, and every thread then scans its lists from there.  The lanes of a warp
 // read the same staged entry at the same time (a broadcast), where the thread-per-query
 // kernels gather the same data through L1 once per lane.
 
