@@ -612,7 +612,8 @@ static int run_query_impl(p2m_index* h, MeshData& m, const float* d_pts, int64_t
     if (v.G == 0) return launch_bvh_closest(v, d_pts, nullptr, nullptr, n, d_dist, d_closest, d_tri, d_bary, index_status(h), s);
     // the site-staged schedule pays when sites have many queries each; a smaller call takes
     // the Morton-ordered thread-per-query path instead
-    if (m.site_staged && n >= 4096 && n >= 48 * (int64_t)v.n_sites)
+    if (m.site_staged && n >= 4096 && n >= 48 * (int64_t)v.n_sites &&
+        (int64_t)v.n_sites * kDqBuckets + 2 <= 0x7fffffffLL)
         return run_query_staged(h, m, d_pts, n, d_dist, d_closest, d_tri, d_bary, counters, rest, s);
     // scratch: rest ids [n], long queue [n] of int2, counters; for the sorted schedules also
     // the sort keys / permutation double buffers [4][n], per-query (query, site) pairs and long
