@@ -110,9 +110,12 @@ def test_noisy_icosphere_small(p2m, aux):
     check_structure(p2m, idx, mesh, q[:2000], n_sites_check=80)
 
 
-def test_cylinder_cone_small(p2m):
+@pytest.mark.parametrize("aux_centre", [1, 0])
+def test_cylinder_cone_small(p2m, aux_centre):
+    """Both placements of the auxiliary centre sites (the centroid of a dense cell's Voronoi
+    vertices, or the cell's centre) give exact results."""
     mesh, q = W.workload_symmetric(20_000, n_ang=48, n_ax=12)
-    idx = p2m.P2MIndex(mesh.verts, mesh.tris)
+    idx = p2m.P2MIndex(mesh.verts, mesh.tris, aux_centre=aux_centre)
     check_parity(mesh, q, _query(idx, q))
     check_structure(p2m, idx, mesh, q[:2000], n_sites_check=80)
 
@@ -165,6 +168,13 @@ def test_counters(p2m):
     c = idx.counters(torch.from_numpy(q).cuda())
     assert c["n_queries"] == 20000 and c["row_entries"] >= c["exact_tests"] > 0
     assert c["site_candidates"] >= 20000 - c["n_outside"]
+    # Table 4's "Queried": the sum of the nearest sites' list lengths, recomputed from the
+    # oracle's nearest sites over the index's own sites (every query lies inside D here)
+    sites, _, _ = idx.sites()
+    off, _ = idx.lists()
+    s_orc, _, _ = oracle.nearest_site(sites.astype(np.float64), q.astype(np.float64))
+    assert c["n_outside"] == 0
+    assert c["queried_list"] == int(np.sum(off[s_orc + 1] - off[s_orc]))
 
 
 @pytest.mark.parametrize("schedule", [1, 2, 3, 4, 5])
