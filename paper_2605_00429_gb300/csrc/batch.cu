@@ -262,14 +262,18 @@ int run_batch_query(p2m_index* h, const float* d_pts, const int64_t* h_off, floa
     a.rec = nullptr;
     unsigned* status = index_status(h);
     if (!b.tuned) {
-        // autotuner: time each (tile, long_row) candidate on this batch, keep the fastest
+        // autotuner: time each (tile, long_row) candidate on this batch, keep the fastest.
+        // long_row starts at the lists' own threshold: the warp pass reads the list-order
+        // bounding spheres, which the build stores only for the lists longer than that
         const int tiles[] = {1024, 4096};
-        const int longs[] = {0, 64, 256, 1024};
+        const int64_t lr0 = h->meshes[0]->long_row;
+        const int longs[] = {(int)lr0, (int)std::min<int64_t>(4 * lr0, 0x7fffffff),
+                             (int)std::min<int64_t>(16 * lr0, 0x7fffffff)};
         Event e0, e1;
         P2M_CUDA_TRY(cudaEventCreate(&e0.e));
         P2M_CUDA_TRY(cudaEventCreate(&e1.e));
         float best = 1e30f;
-        int bt = tiles[0], bl = longs[1];
+        int bt = tiles[0], bl = longs[0];
         for (int tile : tiles) {
             P2M_TRY(make_tiles(b, off, tile));
             a.tiles = b.tiles.as<const int4>();
