@@ -566,9 +566,16 @@ static int run_query_staged(p2m_index* h, MeshData& m, const float* d_pts, int64
     k_site_scatter<<<blocks, threads, 0, s>>>(d_pts, n, key, rank, site_first, qs);
     P2M_CUDA_TRY(cudaGetLastError());
     // queries per thread: up to kStagePer, fewer when the call would not give every resident
-    // block (5 per SM) a tile
+    // block (5 per SM) a tile, and fewer when sites have few queries each, so that a tile
+    // spans no more sites than the staging area holds lists of.  Measured on the icosphere(6)
+    // at 61 / 122 / 244 queries per site: best with 1 / 2 / 4 queries per thread (0.62 /
+    // 1.03 / 1.83 ms, against 0.72 / 1.07 / 1.83 with 4); the cylinder + cone, at 97, is best
+    // with 4.
     const int64_t resident = (int64_t)sm_count() * 5;
-    const int per = (int)std::max<int64_t>(1, std::min<int64_t>(kStagePer, n / (resident * kStageThreads)));
+    const int64_t q_site = n / std::max(S, 1);
+    const int64_t by_site = q_site >= 90 ? kStagePer : (q_site >= 70 ? 2 : 1);
+    const int per = (int)std::max<int64_t>(
+        1, std::min<int64_t>(std::min<int64_t>(kStagePer, n / (resident * kStageThreads)), by_site));
     const int sblocks = (int)std::max<int64_t>(
         1, std::min<int64_t>((n + (int64_t)kStageThreads * per - 1) / ((int64_t)kStageThreads * per), resident * 4));
     timing_mark(h, 1, s);
