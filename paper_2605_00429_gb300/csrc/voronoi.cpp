@@ -36,11 +36,25 @@ void SiteSet::world(int i, double out[3]) const { lat.to_world(pts[i], out); }
 
 int hardware_threads();
 
-// Insert sites [first, pts.size()) into the triangulation in Morton order; a site whose
-// insertion fails (flat tetrahedron or exact duplicate) is moved by one lattice step.
+// Insert sites [first, pts.size()) into the triangulation in a biased randomized insertion
+// order (Amenta, Choi and Rote 2003): each site draws a round, the last round holding about
+// half of them, the one before a quarter, and so on; within a round the sites go in Morton
+// order.  A pure Morton order sweeps the sites of a surface mesh in space, and the
+// triangulation's open front then carries long tetrahedra with huge circumspheres that each
+// new site must cut away.  A site whose insertion fails (flat tetrahedron or exact duplicate)
+// is moved by one lattice step.
 int SiteSet::triangulate_from(int first, uint64_t seed, std::string& err) {
     std::vector<std::pair<uint64_t, int>> order;
-    for (int i = first; i < (int)pts.size(); ++i) order.push_back({morton_key(pts[i], lat.R), i});
+    uint64_t rr = mix64(seed ^ 0xb410ull);
+    for (int i = first; i < (int)pts.size(); ++i) {
+        // round = number of leading one bits of a random word, capped: P(round k) = 2^-(k+1),
+        // reversed so that the big rounds come last
+        rr = mix64(rr);
+        int k = 0;
+        while (k < 20 && ((rr >> k) & 1u)) ++k;
+        const uint64_t round = (uint64_t)(20 - k);
+        order.push_back({(round << 58) | (morton_key(pts[i], lat.R) >> 6), i});
+    }
     std::sort(order.begin(), order.end());
     uint64_t rng = mix64(seed ^ 0x5eedull);
     vid.resize(pts.size(), -1);
