@@ -205,7 +205,9 @@ int p2m_query(p2m_index* h, const float* d_pts, int64_t n, float* d_dist, float*
  * outside a closed, outward-oriented mesh (meaningless for an open or inconsistently
  * oriented one).  d_sdist[n] receives the signed distance; d_closest, d_tri, d_bary as in
  * p2m_query (may be NULL; the index then uses its own scratch for d_tri / d_bary).
- * Asynchronous.  Errors: INVALID_ARG, OOM, CUDA. */
+ * Asynchronous, except that the first call on an index (and the first after
+ * p2m_update_vertices) computes the pseudonormals on the host in FP64 and uploads them
+ * before it launches anything.  Errors: INVALID_ARG, OOM, CUDA. */
 int p2m_query_signed(p2m_index* h, const float* d_pts, int64_t n, float* d_sdist, float* d_closest,
                      int32_t* d_tri, float* d_bary, void* stream);
 

@@ -239,8 +239,9 @@ static int load_mesh(const float* verts, int64_t n_verts, const int32_t* tris, i
 // normal n_f1 + n_f2 of each edge's two faces (a boundary edge keeps its one face's normal),
 // and at every vertex the sum of its faces' normals weighted by their angles there.  The
 // sign of (q - p) . n at the feature (face, edge, vertex) holding the closest point p tells
-// inside from outside on a closed, outward-oriented mesh.
-static int build_pseudonormals(MeshData& m) {
+// inside from outside on a closed, outward-oriented mesh.  Built on the first signed query
+// (only that entry point reads them), not with the index.
+int p2m::build_pseudonormals(MeshData& m) {
     const int64_t T = m.n_tris, V = m.n_verts;
     std::vector<double> fn(3 * T, 0.0), vn(3 * V, 0.0);
     auto vtx = [&](int64_t i, int k) { return (double)m.verts[3 * i + k]; };
@@ -307,9 +308,10 @@ static int build_mesh(MeshData& m, const p2m_build_params& prm, p2m_index* h, cu
         st.domain_lo[k] = m.dom_lo[k];
         st.domain_hi[k] = m.dom_hi[k];
     }
-    // upload + K0b
+    // upload + K0b; the pseudonormals of the signed query are rebuilt on its next call
     const int T = (int)m.n_tris;
-    P2M_TRY(build_pseudonormals(m));
+    m.d_snorm.release();
+    m.d_vnorm.release();
     P2M_TRY(m.d_verts.alloc(sizeof(float) * 3 * m.n_verts));
     P2M_TRY(m.d_tris.alloc(sizeof(int32_t) * 3 * m.n_tris));
     P2M_CUDA_TRY(cudaMemcpyAsync(m.d_verts.p, m.verts.data(), sizeof(float) * 3 * m.n_verts, cudaMemcpyHostToDevice, s));

@@ -81,6 +81,8 @@ void timing_mark(p2m_index* h, int k, cudaStream_t s);
 
 // Sites, Delaunay, augmentation, corner balls, interception lists, nearest-site grid.
 int build_partition(MeshData& m, const p2m_build_params& prm, p2m_index* h, cudaStream_t s);
+// Angle-weighted pseudonormals of the signed query (host FP64, uploaded to m.d_snorm/d_vnorm).
+int build_pseudonormals(MeshData& m);
 
 // Full query of one mesh; counters (8 x u64, may be NULL) accumulate instrumentation.
 int run_query(p2m_index* h, MeshData& m, const float* d_pts, int64_t n, float* d_dist, float* d_closest,

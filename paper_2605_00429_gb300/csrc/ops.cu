@@ -261,6 +261,7 @@ int p2m_query_signed(p2m_index* h, const float* d_pts, int64_t n, float* d_sdist
     P2M_TRY(check_call(h, n, "p2m_query_signed"));
     cudaStream_t s = (cudaStream_t)stream;
     MeshData& m = *h->meshes[0];
+    if (!m.d_snorm.p) P2M_TRY(build_pseudonormals(m));
     // the sign needs the triangle and barycentrics: use the caller's buffers or scratch
     int32_t* tri = d_tri;
     float* bary = d_bary;
