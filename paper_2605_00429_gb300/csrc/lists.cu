@@ -26,6 +26,7 @@ namespace p2m {
 constexpr int kListWarps = 4;     // warps per block
 constexpr int kChunk = 32;        // list entries per chunk box
 constexpr int kListStack = 64;
+constexpr int kStash = 512;       // entries of one item a warp keeps in shared memory (first pass)
 
 __device__ __forceinline__ bool any_ball_box(const float4* __restrict__ balls, int nb, float3 lo, float3 hi) {
     bool hit = false;
@@ -50,18 +51,28 @@ __device__ __forceinline__ bool any_ball_tri(const float4* __restrict__ balls, i
 // right as (parent node, child 0 or 1); a site's list is the concatenation of its items in that
 // order, so one warp never walks the whole tree for a site whose balls cover most of the mesh
 // (the cells reaching the corners of D), and such a site's work spreads over its items' warps.
+// FILL = false: count every item's triangles (count[it]) and, where they fit, keep them: an
+// item of at most kStash triangles is gathered in shared memory and copied to a slot of
+// `stash` reserved with one atomic (item_pos[it] = the slot, or -1 for an item that did not
+// fit), so that the second pass walks the tree again only for the items it must.
+// FILL = true: write every item not kept in the first pass (item_pos[it] < 0) at
+// row_tri[item_off[it] ..].
 template <bool FILL>
 __global__ void __launch_bounds__(32 * kListWarps) k_lists(const float4* __restrict__ balls, const int64_t* __restrict__ ball_off,
                                                             int n_sites, const BNode* __restrict__ nodes, int root,
                                                             const int2* __restrict__ subroots, int n_sub,
                                                             const float4* __restrict__ tri, int64_t* __restrict__ count,
                                                             const int64_t* __restrict__ item_off, int32_t* __restrict__ row_tri,
-                                                            unsigned* status) {
+                                                            int32_t* __restrict__ stash, int64_t stash_cap,
+                                                            unsigned long long* __restrict__ stash_top,
+                                                            int64_t* __restrict__ item_pos, unsigned* status) {
     __shared__ int stk[kListWarps][kListStack];
+    __shared__ int sbuf[FILL ? 1 : kListWarps][FILL ? 1 : kStash];
     const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int nwarps = gridDim.x * kListWarps;
     const int64_t n_items = (int64_t)n_sites * n_sub;
     for (int64_t it = (int64_t)blockIdx.x * kListWarps + w; it < n_items; it += nwarps) {
+        if (FILL && item_pos[it] >= 0) continue;  // kept by the first pass (uniform over the warp)
         const int s = (int)(it / n_sub), r = (int)(it % n_sub);
         const int64_t b0 = ball_off[s];
         const int nb = (int)(ball_off[s + 1] - b0);
@@ -69,7 +80,10 @@ __global__ void __launch_bounds__(32 * kListWarps) k_lists(const float4* __restr
         int64_t k = 0;
         const int64_t out = FILL ? item_off[it] : 0;
         auto emit = [&](int f) {
-            if (FILL && lane == 0) row_tri[out + k] = f;
+            if (lane == 0) {
+                if (FILL) row_tri[out + k] = f;
+                else if (k < kStash) sbuf[FILL ? 0 : w][k] = f;
+            }
             ++k;
         };
         if (nb > 0) {
@@ -134,8 +148,43 @@ __global__ void __launch_bounds__(32 * kListWarps) k_lists(const float4* __restr
                 }
             }
         }
-        if (!FILL && lane == 0) count[it] = k;
+        if (!FILL) {
+            long long pos = -1;
+            if (k <= kStash) {
+                if (lane == 0) {
+                    pos = 0;
+                    if (k > 0) {
+                        pos = (long long)atomicAdd(stash_top, (unsigned long long)k);
+                        if (pos + k > stash_cap) pos = -1;  // the stash is full: the second pass writes it
+                    }
+                }
+                pos = __shfl_sync(0xffffffffu, pos, 0);
+                __syncwarp();
+                if (pos >= 0)
+                    for (int j = lane; j < (int)k; j += 32) stash[pos + j] = sbuf[FILL ? 0 : w][j];
+                __syncwarp();
+            }
+            if (lane == 0) {
+                count[it] = k;
+                item_pos[it] = pos;
+            }
+        }
         if (FILL && lane == 0 && k != item_off[it + 1] - item_off[it]) atomicOr(status, ST_BAD);
+    }
+}
+
+// The items kept by the first pass, from the stash to their places in the lists (a warp per
+// item).
+__global__ void k_copy_stash(const int32_t* __restrict__ stash, const int64_t* __restrict__ item_pos,
+                             const int64_t* __restrict__ item_off, int64_t n_items, int32_t* __restrict__ row_tri) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warp = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+    const int64_t nwarps = ((int64_t)gridDim.x * blockDim.x) >> 5;
+    for (int64_t it = warp; it < n_items; it += nwarps) {
+        const int64_t pos = item_pos[it];
+        if (pos < 0) continue;
+        const int64_t o = item_off[it], k = item_off[it + 1] - o;
+        for (int64_t j = lane; j < k; j += 32) row_tri[o + j] = stash[pos + j];
     }
 }
 
@@ -364,16 +413,24 @@ int build_lists(MeshData& m, const float4* d_balls, const int64_t* d_ball_off, i
     }
     const int n_sub = (int)sub.size();
     const int64_t n_items = (int64_t)n_sites * n_sub;
-    DevBuf d_sub, cnt, item_off, off64, tmp;
+    DevBuf d_sub, cnt, item_off, off64, tmp, stash, item_pos, top;
     P2M_TRY(d_sub.alloc(sizeof(int2) * n_sub));
     P2M_CUDA_TRY(cudaMemcpyAsync(d_sub.p, sub.data(), sizeof(int2) * n_sub, cudaMemcpyHostToDevice, s));
     P2M_TRY(cnt.alloc(sizeof(int64_t) * (n_items + 1)));
     P2M_TRY(item_off.alloc(sizeof(int64_t) * (n_items + 1)));
     P2M_TRY(off64.alloc(sizeof(int64_t) * (n_sites + 1)));
+    // the first pass's stash: room for 64 entries per item on average, at most 2^28 entries
+    const int64_t stash_cap = std::max<int64_t>(1024, std::min<int64_t>(64 * n_items, (int64_t)1 << 28));
+    P2M_TRY(stash.alloc(sizeof(int32_t) * stash_cap));
+    P2M_TRY(item_pos.alloc(sizeof(int64_t) * std::max<int64_t>(n_items, 1)));
+    P2M_TRY(top.alloc(sizeof(unsigned long long)));
+    P2M_CUDA_TRY(cudaMemsetAsync(top.p, 0, sizeof(unsigned long long), s));
     const int blocks = (int)std::max<int64_t>(1, std::min<int64_t>((n_items + kListWarps - 1) / kListWarps,
                                                                    (int64_t)sm_count() * 16));
     k_lists<false><<<blocks, 32 * kListWarps, 0, s>>>(d_balls, d_ball_off, n_sites, v.bvh, v.bvh_root, d_sub.as<int2>(),
-                                                     n_sub, v.tri, cnt.as<int64_t>(), nullptr, nullptr, status);
+                                                     n_sub, v.tri, cnt.as<int64_t>(), nullptr, nullptr,
+                                                     stash.as<int32_t>(), stash_cap, top.as<unsigned long long>(),
+                                                     item_pos.as<int64_t>(), status);
     P2M_CUDA_TRY(cudaGetLastError());
     P2M_CUDA_TRY(cudaMemsetAsync(cnt.as<int64_t>() + n_items, 0, sizeof(int64_t), s));
     size_t tb = 0;
@@ -392,10 +449,15 @@ int build_lists(MeshData& m, const float4* d_balls, const int64_t* d_ball_off, i
     m.nnz = nnz;
     P2M_TRY(m.d_row_tri.alloc(sizeof(int32_t) * std::max<int64_t>(nnz, 1)));
     P2M_TRY(m.d_row_off.alloc(sizeof(int32_t) * (n_sites + 1)));
+    k_copy_stash<<<std::max(1, std::min((int)((n_items + 7) / 8), sm_count() * 16)), 256, 0, s>>>(
+        stash.as<int32_t>(), item_pos.as<int64_t>(), item_off.as<int64_t>(), n_items, m.d_row_tri.as<int32_t>());
+    P2M_CUDA_TRY(cudaGetLastError());
     k_lists<true><<<blocks, 32 * kListWarps, 0, s>>>(d_balls, d_ball_off, n_sites, v.bvh, v.bvh_root, d_sub.as<int2>(),
                                                     n_sub, v.tri, nullptr, item_off.as<int64_t>(),
-                                                    m.d_row_tri.as<int32_t>(), status);
+                                                    m.d_row_tri.as<int32_t>(), nullptr, 0, nullptr,
+                                                    item_pos.as<int64_t>(), status);
     P2M_CUDA_TRY(cudaGetLastError());
+    stash.release();
     k_i64_to_i32<<<64, 256, 0, s>>>(off64.as<int64_t>(), m.d_row_off.as<int32_t>(), n_sites + 1);
     P2M_CUDA_TRY(cudaGetLastError());
     // entry keys; lists scanned per thread are sorted by key (nearest first)
